@@ -1,0 +1,18 @@
+"""CPU oracle for the Jacobi-preconditioned CG path (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product path never does; it shares no code
+with it.
+"""
+
+from .oracle import (  # noqa: F401
+    REASON,
+    build,
+    load,
+    dot,
+    spmv,
+    diagonal,
+    pcg,
+    pcg_f32,
+    ir,
+)
