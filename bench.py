@@ -1,0 +1,455 @@
+"""Benchmark: Jacobi-PCG solves per second on the 128^3 7-point Laplacian.
+
+Workload (the configuration the headline metric is quoted on): 3-D 7-point
+Dirichlet Laplacian on a 128^3 grid, n = 2,097,152, nnz = 14,581,760, CSR
+int32/float64, x_true ~ U[-1,1] (seed 0), b = A x_true, x0 = 0, rtol 1e-8,
+convergence test every 10 iterations, every scalar on the device, the
+iteration captured as a CUDA graph repeated by a device-side while loop.
+
+A step is one complete solve (set-up kernel + all iterations to rtol 1e-8),
+the same work as the paper's timed KSPSolve (Sec. 4.1).  Inputs are resident
+in HBM when the timed region starts; the working set (CSR 175 MB plus five
+16.8 MB vectors) is larger than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl apcg|reference]
+Under torchrun every rank solves its own replica (replicas only: a single
+solve is not sharded), value = total solves / max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG µs/iteration & solves/sec at rtol 1e-8 (async vs host-sync, FP64); HBM GB/s vs peak"
+WORKLOAD = "3D 7-point Laplacian 128^3 (n=2,097,152, nnz=14,581,760), CSR int32/FP64, Jacobi-PCG to rtol 1e-8, check every 10"
+RTOL, K_CHECK, MAX_IT = 1e-8, 10, 5000
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _golden_iters():
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_pcg_history.json")) as f:
+        return int(json.load(f)["c2_full_seed0"]["iters"])
+
+
+class Clocks:
+    """Sample nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+        "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL,
+                text=True,
+            )
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if still current."""
+    try:
+        from paper_2306_17801_gb300 import _build
+
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        if rec.get("source_hash") != _build.source_hash():
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from synthetic import single_problem
+
+    p = single_problem("c2", seed=0)
+    iters_full = _golden_iters()
+    sample_iters = 20  # the paper's fixed-iteration solve (Sec. 4.1)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.pcg(p.A, p.b, rtol=0.0, max_it=sample_iters, check_every=K_CHECK)
+        dt = time.perf_counter() - t0
+        assert r["iters"] == sample_iters
+        if i >= args.warmup:
+            times.append(dt)
+    t_iter = sum(times) / (len(times) * sample_iters)
+    value = 1.0 / (t_iter * iters_full)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_iter * iters_full,
+        "us_per_iteration": 1e6 * t_iter,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "iters_per_solve": iters_full},
+        "cpu_baseline": {
+            "value": value,
+            "unit": "solves/s",
+            "cores": 1,
+            "kind": "oracle",
+            "sample": f"{sample_iters} PCG iterations of the full 128^3 system per step (single-threaded C), "
+            f"scaled by the {iters_full} iterations of a full solve",
+        },
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    _ = np
+
+
+def cpu_baseline_sample():
+    """Time the oracle on a bounded sample (about 10 s of CPU work) of the workload."""
+    import oracle
+    from synthetic import single_problem
+
+    p = single_problem("c2", seed=0)
+    iters_full = _golden_iters()
+    sample_iters = 150
+    t0 = time.perf_counter()
+    r = oracle.pcg(p.A, p.b, rtol=0.0, max_it=sample_iters, check_every=K_CHECK)
+    dt = time.perf_counter() - t0
+    assert r["iters"] == sample_iters
+    t_iter = dt / sample_iters
+    return {
+        "value": 1.0 / (t_iter * iters_full),
+        "unit": "solves/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"{sample_iters} PCG iterations of the full 128^3 system (single-threaded C oracle), "
+        f"scaled by the {iters_full} iterations of a full solve",
+        "us_per_iteration": 1e6 * t_iter,
+    }
+
+
+def run_apcg(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+    from synthetic import single_problem
+    import ctypes as C
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    apcg.load()
+    V = C.c_void_p
+
+    p = single_problem("c2", seed=0)
+    n, nnz = p.n, p.nnz
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rowptr, col, val, b = t(p.A.rowptr), t(p.A.col), t(p.A.val), t(p.b)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = apcg.ctx_create(stream)
+    A = apcg.mat_wrap(rowptr, col, val)
+    vb, vx = apcg.vec_wrap(b), apcg.vec_wrap(x)
+    torch.cuda.synchronize()
+
+    def make_plan(mode, k=K_CHECK):
+        return apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=RTOL, check_every=k, mode=mode, max_it=MAX_IT))
+
+    plan = make_plan("async_graph")
+
+    def step(pl):
+        apcg.call("apcg_vec_set_async", V(ctx), V(vx), C.c_double(0.0))
+        return apcg.cg_plan_solve(pl, vb, vx)
+
+    for _ in range(args.warmup):
+        res = step(plan)
+    assert res["reason"] == "converged", res
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K complete solves, device-timed on the context stream
+    c0 = apcg.get_counters()
+    with Clocks(local) as clk:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iters = []
+        for _ in range(args.steps):
+            r = step(plan)
+            iters.append(r["iters"])
+        e1.record(stream)
+        barrier()
+    c1 = apcg.get_counters()
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    it = iters[-1]
+    value = world * args.steps / (ms_total / 1e3)
+    gpu_launches = c1["kernel_launches"] - c0["kernel_launches"]
+
+    out = {}
+    if rank == 0:
+        # ---- dominant kernel: SpMV + (p,Ap), timed alone on the same stream
+        prof_plan = make_plan("async")
+        apcg.call("apcg_vec_set_async", V(ctx), V(vx), C.c_double(0.0))
+        ms_k = apcg.cg_plan_profile(prof_plan, vb, vx, 30)
+        apcg.call("apcg_cg_plan_destroy", V(prof_plan))
+        bytes_k1 = 12 * nnz + 4 * (n + 1) + 16 * n
+        bytes_k2, bytes_k3 = 56 * n, 32 * n
+        bytes_iter = 12 * nnz + 4 * (n + 1) + 104 * n
+        peak, peak_kind = _peaks()
+        ach = bytes_k1 / (ms_k[0] * 1e-3) / 1e9
+        trec = _traffic_record()
+        out["roofline"] = {
+            "kernel": "cg_spmv_dot_kernel (w = A p, (p,w), alpha)",
+            "bound": "hbm",
+            "achieved": ach,
+            "peak": peak,
+            "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "unit": "GB/s",
+            "frac": ach / peak,
+            "traffic": trec["traffic_bytes_per_launch"] if trec else None,
+            "algorithmic_bytes": bytes_k1,
+            "avg_launch_ms": ms_k[0],
+        }
+        us_iter = 1e3 * ms_step / it
+        out["iteration"] = {
+            "us_per_iteration": us_iter,
+            "kernel_ms": {"spmv_dot": ms_k[0], "update": ms_k[1], "aypx": ms_k[2]},
+            "kernel_GBps": {
+                "spmv_dot": ach,
+                "update": bytes_k2 / (ms_k[1] * 1e-3) / 1e9,
+                "aypx": bytes_k3 / (ms_k[2] * 1e-3) / 1e9,
+            },
+            "algorithmic_bytes_per_iteration": bytes_iter,
+            "GBps_per_iteration": bytes_iter / (us_iter * 1e-6) / 1e9,
+            "frac_of_peak": bytes_iter / (us_iter * 1e-6) / 1e9 / peak,
+        }
+        # ---- host-synchronous and launch-per-kernel forms of the same solve
+        modes = {}
+        for mode in ("host_sync", "async"):
+            pl = make_plan(mode)
+            step(pl)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = step(pl)
+            dt = time.perf_counter() - t0
+            modes[mode] = {"ms_per_solve": 1e3 * dt, "us_per_iteration": 1e6 * dt / r["iters"], "iters": r["iters"]}
+            apcg.call("apcg_cg_plan_destroy", V(pl))
+        modes["async_graph"] = {"ms_per_solve": ms_step, "us_per_iteration": us_iter, "iters": it}
+        modes["speedup_async_graph_vs_host_sync"] = modes["host_sync"]["us_per_iteration"] / us_iter
+        out["modes"] = modes
+        # ---- end to end through the host-buffer entry point (pinned host memory)
+        if not args.no_e2e:
+            hp = {
+                "rowptr": torch.from_numpy(p.A.rowptr).pin_memory(),
+                "col": torch.from_numpy(p.A.col).pin_memory(),
+                "val": torch.from_numpy(p.A.val).pin_memory(),
+                "b": torch.from_numpy(p.b).pin_memory(),
+            }
+            xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+            opts = apcg.cg_opts(rtol=RTOL, check_every=K_CHECK, mode="async_graph", max_it=MAX_IT)
+
+            def host_step():
+                xh.zero_()
+                res = apcg.CgResult()
+                apcg.call(
+                    "apcg_cg_solve_host", n, nnz, V(hp["rowptr"].data_ptr()), V(hp["col"].data_ptr()),
+                    V(hp["val"].data_ptr()), V(hp["b"].data_ptr()), V(xh.data_ptr()), C.byref(opts), C.byref(res),
+                )
+                return res
+
+            for _ in range(2):
+                host_step()
+            ks = max(3, args.steps // 2)
+            t0 = time.perf_counter()
+            for _ in range(ks):
+                rr = host_step()
+            dt = (time.perf_counter() - t0) / ks
+            assert rr.reason == 0
+            h2d = sum(v.numel() * v.element_size() for v in hp.values()) + xh.numel() * 8
+            out["e2e"] = {"value": 1.0 / dt, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8, "ms_per_step": 1e3 * dt}
+        # ---- the oracle on the host cores
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_sample()
+        # ---- the small case: 64^2 5-point, host-sync vs async forms (k = 1)
+        out["small_case"] = small_case(apcg, ctx, dev)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "solves/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "us_per_iteration": 1e3 * ms_step / it,
+            "iters_per_solve": it,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {
+                "workload": WORKLOAD,
+                "n": n,
+                "nnz": nnz,
+                "mode": "async_graph",
+                "parallelism": "replicas" if world > 1 else "single",
+                "l2": "inputs larger than L2 (CSR 175 MB + 5 x 16.8 MB vectors), no flush",
+            },
+            "clocks": clk.summary(),
+            "gpu_launches": gpu_launches,
+            **out,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def small_case(apcg, ctx, dev):
+    """64x64 5-point Laplacian, rtol 1e-8, convergence test every iteration."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from synthetic import single_problem
+
+    V = C.c_void_p
+    p = single_problem("c1", seed=0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rowptr, col, val, b = t(p.A.rowptr), t(p.A.col), t(p.A.val), t(p.b)
+    x = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    A = apcg.mat_wrap(rowptr, col, val)
+    vb, vx = apcg.vec_wrap(b), apcg.vec_wrap(x)
+    out = {"workload": "2D 5-point Laplacian 64^2 (n=4096, nnz=20,224), rtol 1e-8, k=1"}
+    for mode in ("host_sync", "async", "async_graph"):
+        pl = apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=1e-8, check_every=1, mode=mode))
+        best = None
+        for _ in range(5):
+            apcg.call("apcg_vec_set_async", V(ctx), V(vx), C.c_double(0.0))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = apcg.cg_plan_solve(pl, vb, vx)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        out[mode] = {"us_per_iteration": 1e6 * best / r["iters"], "iters": r["iters"], "ms_per_solve": 1e3 * best}
+        apcg.call("apcg_cg_plan_destroy", V(pl))
+    out["speedup_async_graph_vs_host_sync"] = out["host_sync"]["us_per_iteration"] / out["async_graph"]["us_per_iteration"]
+    for h in (vb, vx):
+        apcg.call("apcg_vec_destroy", V(h))
+    apcg.call("apcg_mat_destroy", V(A))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["apcg", "reference"], default="apcg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = _env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        # other ranks wait for rank 0's build
+        deadline = time.time() + 600
+        from paper_2306_17801_gb300 import _build
+
+        while not _build.up_to_date() and time.time() < deadline:
+            time.sleep(1)
+    run_apcg(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,418 @@
+/*
+ * apcg.h -- asynchronous device-scalar Jacobi-preconditioned CG for NVIDIA GB300.
+ *
+ * C ABI of libapcg.so.  Every call returns an apcg_status (0 = success,
+ * negative = error), the convention of the paper's footnote to the core
+ * stream-control listing (Sec. 3.1.1: every routine returns an error code).
+ * On error, apcg_last_error_string() gives a per-thread message.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Pointers called "device" must point to memory the current CUDA device can
+ *   read (cudaMalloc, cudaMallocAsync or PyTorch CUDA tensors); pointers called
+ *   "host" must be ordinary host memory.  float64 vectors must be 16-byte
+ *   aligned, float32 vectors 16-byte aligned as well (every CUDA and PyTorch
+ *   allocation is).  Misaligned pointers return APCG_ERR_INVALID_ARG.
+ * - The library never owns caller buffers.  apcg_vec / apcg_mat are
+ *   non-owning views; the caller keeps the memory alive until the work that
+ *   uses it has finished (apcg_ctx_synchronize, or a host accessor).
+ * - Handles (contexts, scalars, vectors, matrices, plans) are owned by the
+ *   caller and released with the matching *_destroy.  A destroy never
+ *   blocks: device memory behind a handle is released only once every stream
+ *   that used it is idle (Sec. 3.2.2, lifetime of managed objects).
+ * - Arguments are validated before anything is enqueued.  Errors that arise
+ *   on the device (a breakdown, a non-finite value, a bad diagonal) are
+ *   recorded on the device and reported by the next call that synchronizes
+ *   (a host accessor, apcg_ctx_synchronize, or a solver's result).
+ * - A context argument of NULL selects the library's global-blocking
+ *   context: the call waits for all prior work on every context and has
+ *   completed when it returns (Sec. 3.1, global-blocking streams; Sec. 3.2.2,
+ *   an Eval without a context).
+ * - Thread safety: all entry points may be called from several host threads;
+ *   operations on one context are ordered by the order of the calls.
+ */
+#ifndef APCG_H
+#define APCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define APCG_API __attribute__((visibility("default")))
+#else
+#define APCG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+
+typedef int32_t apcg_status;
+
+#define APCG_OK 0
+#define APCG_ERR_INVALID_ARG (-1)  /* bad handle, size, pointer or alignment */
+#define APCG_ERR_CUDA (-2)         /* a CUDA runtime call failed (message has the CUDA error) */
+#define APCG_ERR_NO_MEMORY (-3)    /* device or host allocation failed */
+#define APCG_ERR_BAD_DIAGONAL (-4) /* Jacobi: a diagonal entry is missing, zero or not finite */
+#define APCG_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
+#define APCG_ERR_UNSUPPORTED (-6)  /* valid request that this build does not support */
+#define APCG_ERR_NOT_READY (-7)    /* query only: work still pending (never an error elsewhere) */
+#define APCG_ERR_BREAKDOWN (-8)    /* a solver met (p, Ap) <= 0 or a non-finite value */
+
+/* Message of the last failing call on this host thread (never NULL). */
+APCG_API const char* apcg_last_error_string(void);
+/* Library version as major*10000 + minor*100 + patch. */
+APCG_API int32_t apcg_version(void);
+
+/* ------------------------------------------------------------------ handles */
+
+typedef struct apcg_ctx_s* apcg_ctx;
+typedef struct apcg_scalar_s* apcg_scalar;
+typedef struct apcg_vec_s* apcg_vec;
+typedef struct apcg_mat_s* apcg_mat;
+typedef struct apcg_cg_plan_s* apcg_cg_plan;
+typedef uint64_t apcg_id;
+
+typedef enum {
+  APCG_STREAM_DEFAULT_BLOCKING = 0, /* asynchronous w.r.t. the host and every other context */
+  APCG_STREAM_GLOBAL_BLOCKING = 1   /* waits for all prior work on every context, and
+                                       completes before the launching call returns */
+} apcg_stream_type;
+
+typedef enum { APCG_ACCESS_READ = 1, APCG_ACCESS_WRITE = 2, APCG_ACCESS_READ_WRITE = 3 } apcg_access;
+
+typedef enum {
+  APCG_JOIN_DESTROY = 0, /* parent waits on every child, then the children are destroyed */
+  APCG_JOIN_SYNC = 1,    /* parent waits on every child, then every child waits on the parent */
+  APCG_JOIN_NO_SYNC = 2  /* parent waits on every child; children continue independently */
+} apcg_join_mode;
+
+typedef enum { APCG_F64 = 0, APCG_F32 = 1 } apcg_dtype;
+
+/* ------------------------------------------------------------------ device contexts (Sec. 3.1) */
+
+/*
+ * Create a context on the current CUDA device owning a new non-blocking
+ * stream (Sec. 3.1: a context is a device plus the stream it manages).
+ * Stream type: APCG_STREAM_DEFAULT_BLOCKING.
+ */
+APCG_API apcg_status apcg_ctx_create(apcg_ctx* out);
+
+/*
+ * Create a context that borrows an existing CUDA stream (for example a
+ * PyTorch stream), passed as its cudaStream_t value.  The stream is never
+ * destroyed by the library and must outlive the context.
+ */
+APCG_API apcg_status apcg_ctx_create_from_stream(void* cuda_stream, apcg_ctx* out);
+
+/* Select the stream type (Sec. 3.1).  Takes effect for the next call on the context. */
+APCG_API apcg_status apcg_ctx_set_stream_type(apcg_ctx ctx, apcg_stream_type type);
+APCG_API apcg_status apcg_ctx_get_stream_type(apcg_ctx ctx, apcg_stream_type* type);
+
+/*
+ * The cudaStream_t of the context, for launching caller kernels between
+ * apcg_mark_intent_begin/end (marking listing example, Sec. 3.1.2).  The
+ * caller must not destroy it or change its attributes.
+ */
+APCG_API apcg_status apcg_ctx_get_stream(apcg_ctx ctx, void** cuda_stream);
+
+/*
+ * Core stream control (listing "Core PetscDeviceContext Stream Control APIs",
+ * Sec. 3.1.1): make `waiter` wait for all work enqueued on `waitee` so far;
+ * ask whether all work of a context has finished (*idle = 1) without
+ * blocking; block the host until all work of a context has finished.
+ * apcg_ctx_synchronize also reports device-side errors recorded by work on
+ * the context.
+ */
+APCG_API apcg_status apcg_ctx_wait_for_context(apcg_ctx waiter, apcg_ctx waitee);
+APCG_API apcg_status apcg_ctx_query_idle(apcg_ctx ctx, int32_t* idle);
+APCG_API apcg_status apcg_ctx_synchronize(apcg_ctx ctx);
+
+/*
+ * Fork and join (named among the paper's keywords; the paper does not spell
+ * out their semantics, this is the library's reading): fork creates n child
+ * contexts on the parent's device, with the parent's stream type, whose
+ * streams start after everything enqueued on the parent so far.  Join makes
+ * the parent wait for everything enqueued on each child, then applies `mode`.
+ */
+APCG_API apcg_status apcg_ctx_fork(apcg_ctx parent, int32_t n, apcg_ctx* children);
+APCG_API apcg_status apcg_ctx_join(apcg_ctx parent, int32_t n, apcg_ctx* children, apcg_join_mode mode);
+
+/* Destroy a context.  Pending work still completes; its stream is released afterwards. */
+APCG_API apcg_status apcg_ctx_destroy(apcg_ctx ctx);
+
+/* ------------------------------------------------------------------ memory IDs and intent marking (Sec. 3.1.2) */
+
+/*
+ * Register a memory region and obtain its object ID (listing "Memory
+ * Registration API").  Registering a pointer that is already registered
+ * returns the existing ID.  `ptr` may be a host or device address; `bytes`
+ * is the size of the region.
+ */
+APCG_API apcg_status apcg_register_memory(const void* ptr, size_t bytes, apcg_id* id);
+/* Look up the ID and size of a registered pointer (start address only). */
+APCG_API apcg_status apcg_get_pointer_attributes(const void* ptr, apcg_id* id, size_t* bytes);
+/* Forget a registration; pending marks on it still complete. */
+APCG_API apcg_status apcg_unregister_memory(const void* ptr);
+
+/*
+ * Intent marking (listing "API For Marking Stream Dependencies"): bracket
+ * every launch that accesses object `id` on context `ctx`.  Begin makes the
+ * context's stream wait on exactly the earlier conflicting accesses made on
+ * other contexts: the last write for a read; the last write and every read
+ * since it for a write.  Same-context accesses keep program order and need
+ * no wait; two reads are never ordered (the strong write-ordering rule,
+ * Sec. 3.1.2).  End records the access.  `desc` is for debugging and may be
+ * NULL.  Begin/end pairs for several IDs may be interleaved around one
+ * launch.
+ */
+APCG_API apcg_status apcg_mark_intent_begin(apcg_ctx ctx, apcg_id id, apcg_access mode, const char* desc);
+APCG_API apcg_status apcg_mark_intent_end(apcg_ctx ctx, apcg_id id, apcg_access mode, const char* desc);
+
+/*
+ * Host access to an object (the implicit synchronisation of accessors such
+ * as VecGetArray, Sec. 3.3): block the host only until the accesses that
+ * conflict with `mode` have finished -- the last write for a read, the last
+ * write and all later reads for a write.
+ */
+APCG_API apcg_status apcg_host_access(apcg_id id, apcg_access mode);
+
+/* ------------------------------------------------------------------ counters (profiling) */
+
+typedef struct {
+  int64_t kernel_launches;  /* kernels enqueued by the library (graph launches count their kernels) */
+  int64_t graph_launches;   /* CUDA graph launches */
+  int64_t waits_inserted;   /* cross-context event waits enqueued by marking */
+  int64_t waits_elided;     /* conflicting accesses that needed no wait (already ordered or complete) */
+  int64_t events_recorded;  /* events recorded at the end of marked launches */
+  int64_t host_syncs;       /* host blocking points (accessors, synchronize, global-blocking calls) */
+  int64_t d2h_copies;       /* device-to-host copies */
+  int64_t d2h_bytes;
+  int64_t h2d_copies;       /* host-to-device copies */
+  int64_t h2d_bytes;
+} apcg_counters;
+
+APCG_API apcg_status apcg_get_counters(apcg_counters* out);
+APCG_API apcg_status apcg_reset_counters(void);
+
+/* ------------------------------------------------------------------ managed device scalars (Sec. 3.2) */
+
+/*
+ * A managed scalar is one float64 value that lives in device memory (a slot
+ * of the library's scalar pool) and carries an object ID, so that producers
+ * and consumers on different contexts are ordered by marking (Sec. 3.2: a
+ * future for a value that stays on the device).  Only APCG_F64 is supported.
+ * Creation enqueues nothing; the value is undefined until written.
+ */
+APCG_API apcg_status apcg_scalar_create(apcg_dtype dtype, apcg_scalar* out);
+/* Enqueue value := v on ctx. */
+APCG_API apcg_status apcg_scalar_set_async(apcg_ctx ctx, apcg_scalar s, double v);
+/*
+ * Host accessor (front() in the mixed-API CG example, Sec. 3.3): waits only
+ * for the last write of the scalar, then copies it to *v.
+ */
+APCG_API apcg_status apcg_scalar_get(apcg_scalar s, double* v);
+/* Device address of the slot (valid until apcg_scalar_destroy). */
+APCG_API apcg_status apcg_scalar_device_ptr(apcg_scalar s, double** dptr);
+/* The scalar's object ID, for apcg_mark_intent_* around caller kernels. */
+APCG_API apcg_status apcg_scalar_id(apcg_scalar s, apcg_id* id);
+
+/*
+ * Scalar arithmetic evaluated on the device (what Eval(expr, dctx) launches,
+ * Sec. 3.2.1-3.2.2): out := num / den, out := 1 / a, out := -a, out := a,
+ * out := a * b, out := sqrt(a).  `out` may alias an input.
+ */
+APCG_API apcg_status apcg_scalar_div_async(apcg_ctx ctx, apcg_scalar out, apcg_scalar num, apcg_scalar den);
+APCG_API apcg_status apcg_scalar_recip_async(apcg_ctx ctx, apcg_scalar out, apcg_scalar a);
+APCG_API apcg_status apcg_scalar_neg_async(apcg_ctx ctx, apcg_scalar out, apcg_scalar a);
+APCG_API apcg_status apcg_scalar_copy_async(apcg_ctx ctx, apcg_scalar out, apcg_scalar a);
+APCG_API apcg_status apcg_scalar_mul_async(apcg_ctx ctx, apcg_scalar out, apcg_scalar a, apcg_scalar b);
+APCG_API apcg_status apcg_scalar_sqrt_async(apcg_ctx ctx, apcg_scalar out, apcg_scalar a);
+
+/* Release the scalar; its slot is reused only after every access to it has finished. */
+APCG_API apcg_status apcg_scalar_destroy(apcg_scalar s);
+
+/* ------------------------------------------------------------------ vectors and matrices */
+
+/*
+ * Non-owning view of n contiguous elements at device pointer `dptr`
+ * (Vec, Sec. 3.1.2).  The memory is registered (apcg_register_memory) and
+ * the view takes that object ID.  n may be 0.
+ */
+APCG_API apcg_status apcg_vec_wrap(void* dptr, int64_t n, apcg_dtype dtype, apcg_vec* out);
+APCG_API apcg_status apcg_vec_id(apcg_vec v, apcg_id* id);
+APCG_API apcg_status apcg_vec_destroy(apcg_vec v);
+
+/*
+ * Non-owning view of a square or rectangular CSR matrix (AIJ, Sec. 4.1) in
+ * device memory: rowptr[nrows+1] (int32, rowptr[0] = 0, non-decreasing),
+ * col[nnz] (int32 in [0, ncols)), val[nnz] of `dtype`.  Column indices
+ * need not be sorted, but the row sums are formed in storage order.  The
+ * structure is not checked on the device unless apcg_mat_validate is called.
+ */
+APCG_API apcg_status apcg_mat_csr_wrap(const int32_t* rowptr, const int32_t* col, const void* val, int32_t nrows,
+                              int32_t ncols, int64_t nnz, apcg_dtype dtype, apcg_mat* out);
+/* Check the structure on the host (copies the arrays back): rowptr monotone, columns in range. */
+APCG_API apcg_status apcg_mat_validate(apcg_mat A);
+APCG_API apcg_status apcg_mat_id(apcg_mat A, apcg_id* id);
+APCG_API apcg_status apcg_mat_destroy(apcg_mat A);
+
+/* ------------------------------------------------------------------ asynchronous vector / matrix operations (Sec. 3.3) */
+
+/*
+ * The *Async operations of Sec. 3.3 (VecDotAsync, VecNormAsync,
+ * VecAXPYAsync, VecAYPX, VecScaleAsync, VecCopy, KSP_MatMultAsync,
+ * KSP_PCApplyAsync).  Scalars are managed scalars read or written on the
+ * device; each call marks its operands (read for inputs, write for outputs)
+ * on `ctx` and enqueues one kernel.  Vectors must have equal lengths and
+ * dtypes; only APCG_F64 vectors are supported by these generic operations.
+ * Reductions are deterministic for a given length (fixed two-level order).
+ */
+APCG_API apcg_status apcg_vec_dot_async(apcg_ctx ctx, apcg_vec x, apcg_vec y, apcg_scalar out);    /* out := x'y */
+APCG_API apcg_status apcg_vec_norm2_async(apcg_ctx ctx, apcg_vec x, apcg_scalar out);              /* out := ||x||_2 */
+APCG_API apcg_status apcg_vec_axpy_async(apcg_ctx ctx, apcg_vec y, apcg_scalar a, int32_t negate,  /* y := y + (+-a) x */
+                                apcg_vec x);
+APCG_API apcg_status apcg_vec_aypx_async(apcg_ctx ctx, apcg_vec y, apcg_scalar b, apcg_vec x);     /* y := x + b y */
+APCG_API apcg_status apcg_vec_scale_async(apcg_ctx ctx, apcg_vec y, apcg_scalar a);                /* y := a y */
+APCG_API apcg_status apcg_vec_copy_async(apcg_ctx ctx, apcg_vec dst, apcg_vec src);                /* dst := src */
+APCG_API apcg_status apcg_vec_set_async(apcg_ctx ctx, apcg_vec y, double v);                       /* y := v */
+APCG_API apcg_status apcg_vec_pointwise_mult_async(apcg_ctx ctx, apcg_vec w, apcg_vec x,           /* w := x .* y */
+                                          apcg_vec y);
+
+/* y := A x (MatMult).  x has ncols elements, y has nrows; x and y must not alias. */
+APCG_API apcg_status apcg_mat_mult_async(apcg_ctx ctx, apcg_mat A, apcg_vec x, apcg_vec y);
+/* y := A x and out := x'y in one kernel (square A): the SpMV and the dot that follows it in CG. */
+APCG_API apcg_status apcg_mat_mult_dot_async(apcg_ctx ctx, apcg_mat A, apcg_vec x, apcg_vec y, apcg_scalar out);
+
+/*
+ * Jacobi preconditioner (Sec. 4.1, diagonal scaling): setup writes
+ * dinv := 1 ./ diag(A) (a missing diagonal entry counts as zero; a zero or
+ * non-finite diagonal makes the next synchronizing call on ctx return
+ * APCG_ERR_BAD_DIAGONAL); apply writes z := dinv .* r.
+ */
+APCG_API apcg_status apcg_pc_jacobi_setup_async(apcg_ctx ctx, apcg_mat A, apcg_vec dinv);
+APCG_API apcg_status apcg_pc_jacobi_apply_async(apcg_ctx ctx, apcg_vec dinv, apcg_vec r, apcg_vec z);
+
+/* ------------------------------------------------------------------ conjugate gradient solver (Sec. 3.3, Sec. 4.2) */
+
+typedef enum {
+  /* Scalars go to the host every iteration: (p,Ap) and (r,z),(r,r) are copied
+     back and waited for, alpha and beta are computed on the host and passed
+     by value -- the host-synchronous form the paper benchmarks against. */
+  APCG_MODE_HOST_SYNC = 0,
+  /* All scalars stay on the device; kernels are enqueued back to back and the
+     host reads a 'done' flag once every check_every iterations. */
+  APCG_MODE_ASYNC = 1,
+  /* As ASYNC, with check_every iterations captured once as a CUDA graph and
+     repeated by a device-side while loop (conditional graph node): one graph
+     launch per solve and no host read until the solve ends. */
+  APCG_MODE_ASYNC_GRAPH = 2,
+  /* The whole solve in one kernel on one thread block (small systems). */
+  APCG_MODE_PERSISTENT = 3,
+  /* Library choice: PERSISTENT for small systems, ASYNC_GRAPH otherwise. */
+  APCG_MODE_AUTO = 4
+} apcg_mode;
+
+typedef enum { APCG_CONVERGED = 0, APCG_NOT_CONVERGED = 1, APCG_BREAKDOWN = 2 } apcg_reason;
+
+typedef struct {
+  double rtol;          /* stop when ||r||_2 <= max(rtol * ||b||_2, atol) */
+  double atol;
+  int32_t max_it;       /* iteration cap; <= 0 selects 10 * n */
+  int32_t check_every;  /* k: the test runs when the iteration count is a multiple of k (and at max_it); >= 1 */
+  int32_t mode;         /* apcg_mode */
+  int32_t history_len;  /* number of alpha/beta values to record (0 = none) */
+  double* alpha_hist;   /* host [history_len] or NULL: alpha of iteration i at index i-1 */
+  double* beta_hist;    /* host [history_len] or NULL: beta computed at the end of iteration i */
+} apcg_cg_opts;
+
+/* Fill opts with rtol 1e-8, atol 0, max_it 0, check_every 1, mode AUTO, no history. */
+APCG_API apcg_status apcg_cg_opts_default(apcg_cg_opts* opts);
+
+typedef struct {
+  int32_t iters;            /* completed iterations */
+  int32_t reason;           /* apcg_reason */
+  double rr;                /* (r,r) of the recursively updated residual at exit */
+  double bnorm;             /* ||b||_2 */
+  double rel_res;           /* sqrt(rr) / bnorm (sqrt(rr) when b = 0) */
+  int64_t kernel_launches;  /* kernels this solve executed on the device */
+} apcg_cg_result;
+
+/*
+ * Solve A x = b by Jacobi-PCG (textbook Hestenes-Stiefel CG with diagonal
+ * scaling, Sec. 4.1-4.2; loop body in the order of the mixed-API CG example
+ * of Sec. 3.3, with the standard initialisation r = b - A x0, z = D^-1 r,
+ * p = z).  A is square float64 with a nonzero diagonal; x holds x0 on entry
+ * and the iterate on exit.  Marks A and b read, x read-write.  Blocks the
+ * host once, at the end, to fill *res.  Returns APCG_ERR_BAD_DIAGONAL for a
+ * zero, missing or non-finite diagonal entry, and APCG_OK otherwise (a
+ * breakdown or the iteration cap is reported in res->reason).
+ */
+APCG_API apcg_status apcg_cg_solve(apcg_ctx ctx, apcg_mat A, apcg_vec b, apcg_vec x, const apcg_cg_opts* opts,
+                          apcg_cg_result* res);
+
+/*
+ * Reusable solver plan: set-up once per matrix and option set (Jacobi
+ * diagonal, workspace, launch shapes, captured graphs), then any number of
+ * solves.  The plan keeps non-owning references to A.  A plan's solves on
+ * one context are ordered; the plan must not be used from two contexts at
+ * once.
+ */
+APCG_API apcg_status apcg_cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, apcg_cg_plan* out);
+APCG_API apcg_status apcg_cg_plan_solve(apcg_cg_plan plan, apcg_vec b, apcg_vec x, apcg_cg_result* res);
+/*
+ * Enqueue a solve without waiting for it: the result stays on the device
+ * until apcg_cg_plan_result() is called (which blocks until the solve ends).
+ * History recording is not available through this pair.
+ */
+APCG_API apcg_status apcg_cg_plan_solve_async(apcg_cg_plan plan, apcg_vec b, apcg_vec x);
+APCG_API apcg_status apcg_cg_plan_result(apcg_cg_plan plan, apcg_cg_result* res);
+APCG_API apcg_status apcg_cg_plan_destroy(apcg_cg_plan plan);
+
+/*
+ * Kernel timing for performance reports: runs the set-up kernel once, then
+ * `iters` iterations with each of the three iteration kernels launched on its
+ * own between CUDA events recorded on the plan's context stream, and returns
+ * their average durations in milliseconds (ms[0] = SpMV + (p,Ap), ms[1] =
+ * updates + Jacobi + (r,z),(r,r), ms[2] = search-direction update).  The
+ * iterations run regardless of convergence (iters must not exceed the
+ * iteration count at which the system would break down: use a count well
+ * below its convergence count).  x is overwritten with the iterate reached.
+ */
+APCG_API apcg_status apcg_cg_plan_profile(apcg_cg_plan plan, apcg_vec b, apcg_vec x, int32_t iters, float* ms);
+
+/*
+ * The same solve for callers that hold the system in ordinary host memory:
+ * copies rowptr/col/val/b/x to the device, solves on a library context, and
+ * copies x back.  The copies are part of the call.
+ */
+APCG_API apcg_status apcg_cg_solve_host(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const double* val,
+                               const double* b, double* x, const apcg_cg_opts* opts, apcg_cg_result* res);
+
+/* ------------------------------------------------------------------ host-only simulation of the marking rules */
+
+/*
+ * A simulator of intent marking that never touches a GPU, driving the same
+ * dependency tracker as the real contexts.  It exists so that the ordering
+ * rules of Sec. 3.1.2 can be tested on machines without a GPU.  Contexts are
+ * numbered 0..nctx-1; each apcg_sim_op is one launch that accesses `nids`
+ * objects with the given modes; each simulated launch gets sequence number
+ * 1, 2, ... on its context.  apcg_sim_complete marks every launch of `ctx`
+ * with sequence <= seq as finished.  The log lists the waits the tracker
+ * inserted as "w<-c@s" (context w waits for launch s of context c), one per
+ * line, and the elided ones as "w..c@s".
+ */
+typedef struct apcg_sim_s* apcg_sim;
+APCG_API apcg_status apcg_sim_create(int32_t nctx, apcg_sim* out);
+APCG_API apcg_status apcg_sim_op(apcg_sim sim, int32_t ctx, int32_t nids, const apcg_id* ids, const int32_t* modes);
+APCG_API apcg_status apcg_sim_complete(apcg_sim sim, int32_t ctx, uint64_t seq);
+APCG_API apcg_status apcg_sim_log(apcg_sim sim, char* buf, size_t len);
+APCG_API apcg_status apcg_sim_destroy(apcg_sim sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APCG_H */

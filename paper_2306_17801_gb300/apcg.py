@@ -1,0 +1,451 @@
+"""Thin ctypes binding of libapcg (include/apcg.h).
+
+Argument marshalling only: every entry point keeps its C name; device arrays
+are passed as raw pointers taken from PyTorch CUDA tensors.  All computation
+runs in the library's CUDA kernels.  Importing this module does not need a
+GPU; loading the library needs it to have been built (``build()`` of the
+repository's entry module) and raises ``ImportError`` otherwise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libapcg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "apcg.h")
+
+OK = 0
+ERR = {
+    -1: "APCG_ERR_INVALID_ARG",
+    -2: "APCG_ERR_CUDA",
+    -3: "APCG_ERR_NO_MEMORY",
+    -4: "APCG_ERR_BAD_DIAGONAL",
+    -5: "APCG_ERR_TIMEOUT",
+    -6: "APCG_ERR_UNSUPPORTED",
+    -7: "APCG_ERR_NOT_READY",
+    -8: "APCG_ERR_BREAKDOWN",
+}
+STREAM_DEFAULT_BLOCKING, STREAM_GLOBAL_BLOCKING = 0, 1
+READ, WRITE, READ_WRITE = 1, 2, 3
+JOIN_DESTROY, JOIN_SYNC, JOIN_NO_SYNC = 0, 1, 2
+F64, F32 = 0, 1
+MODE_HOST_SYNC, MODE_ASYNC, MODE_ASYNC_GRAPH, MODE_PERSISTENT, MODE_AUTO = 0, 1, 2, 3, 4
+MODES = {"host_sync": 0, "async": 1, "async_graph": 2, "persistent": 3, "auto": 4}
+REASONS = {0: "converged", 1: "not_converged", 2: "breakdown"}
+
+
+class ApcgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{ERR.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Counters(C.Structure):
+    _fields_ = [
+        (n, C.c_int64)
+        for n in (
+            "kernel_launches",
+            "graph_launches",
+            "waits_inserted",
+            "waits_elided",
+            "events_recorded",
+            "host_syncs",
+            "d2h_copies",
+            "d2h_bytes",
+            "h2d_copies",
+            "h2d_bytes",
+        )
+    ]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class CgOpts(C.Structure):
+    _fields_ = [
+        ("rtol", C.c_double),
+        ("atol", C.c_double),
+        ("max_it", C.c_int32),
+        ("check_every", C.c_int32),
+        ("mode", C.c_int32),
+        ("history_len", C.c_int32),
+        ("alpha_hist", C.POINTER(C.c_double)),
+        ("beta_hist", C.POINTER(C.c_double)),
+    ]
+
+
+class CgResult(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32),
+        ("reason", C.c_int32),
+        ("rr", C.c_double),
+        ("bnorm", C.c_double),
+        ("rel_res", C.c_double),
+        ("kernel_launches", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {
+            "iters": int(self.iters),
+            "reason": REASONS.get(int(self.reason), int(self.reason)),
+            "rr": float(self.rr),
+            "bnorm": float(self.bnorm),
+            "rel_res": float(self.rel_res),
+            "kernel_launches": int(self.kernel_launches),
+        }
+
+
+P = C.c_void_p
+PP = C.POINTER(C.c_void_p)
+S = C.c_int32
+i32, i64, u64, f64 = C.c_int32, C.c_int64, C.c_uint64, C.c_double
+
+# name -> argument types (every function returns apcg_status unless listed in _RESTYPE)
+PROTOS = {
+    "apcg_last_error_string": [],
+    "apcg_version": [],
+    "apcg_get_counters": [C.POINTER(Counters)],
+    "apcg_reset_counters": [],
+    "apcg_ctx_create": [PP],
+    "apcg_ctx_create_from_stream": [P, PP],
+    "apcg_ctx_set_stream_type": [P, C.c_int],
+    "apcg_ctx_get_stream_type": [P, C.POINTER(C.c_int)],
+    "apcg_ctx_get_stream": [P, PP],
+    "apcg_ctx_wait_for_context": [P, P],
+    "apcg_ctx_query_idle": [P, C.POINTER(i32)],
+    "apcg_ctx_synchronize": [P],
+    "apcg_ctx_fork": [P, i32, PP],
+    "apcg_ctx_join": [P, i32, PP, C.c_int],
+    "apcg_ctx_destroy": [P],
+    "apcg_register_memory": [P, C.c_size_t, C.POINTER(u64)],
+    "apcg_get_pointer_attributes": [P, C.POINTER(u64), C.POINTER(C.c_size_t)],
+    "apcg_unregister_memory": [P],
+    "apcg_mark_intent_begin": [P, u64, C.c_int, C.c_char_p],
+    "apcg_mark_intent_end": [P, u64, C.c_int, C.c_char_p],
+    "apcg_host_access": [u64, C.c_int],
+    "apcg_scalar_create": [C.c_int, PP],
+    "apcg_scalar_set_async": [P, P, f64],
+    "apcg_scalar_get": [P, C.POINTER(f64)],
+    "apcg_scalar_device_ptr": [P, PP],
+    "apcg_scalar_id": [P, C.POINTER(u64)],
+    "apcg_scalar_div_async": [P, P, P, P],
+    "apcg_scalar_recip_async": [P, P, P],
+    "apcg_scalar_neg_async": [P, P, P],
+    "apcg_scalar_copy_async": [P, P, P],
+    "apcg_scalar_mul_async": [P, P, P, P],
+    "apcg_scalar_sqrt_async": [P, P, P],
+    "apcg_scalar_destroy": [P],
+    "apcg_vec_wrap": [P, i64, C.c_int, PP],
+    "apcg_vec_id": [P, C.POINTER(u64)],
+    "apcg_vec_destroy": [P],
+    "apcg_mat_csr_wrap": [P, P, P, i32, i32, i64, C.c_int, PP],
+    "apcg_mat_validate": [P],
+    "apcg_mat_id": [P, C.POINTER(u64)],
+    "apcg_mat_destroy": [P],
+    "apcg_vec_dot_async": [P, P, P, P],
+    "apcg_vec_norm2_async": [P, P, P],
+    "apcg_vec_axpy_async": [P, P, P, i32, P],
+    "apcg_vec_aypx_async": [P, P, P, P],
+    "apcg_vec_scale_async": [P, P, P],
+    "apcg_vec_copy_async": [P, P, P],
+    "apcg_vec_set_async": [P, P, f64],
+    "apcg_vec_pointwise_mult_async": [P, P, P, P],
+    "apcg_mat_mult_async": [P, P, P, P],
+    "apcg_mat_mult_dot_async": [P, P, P, P, P],
+    "apcg_pc_jacobi_setup_async": [P, P, P],
+    "apcg_pc_jacobi_apply_async": [P, P, P, P],
+    "apcg_cg_opts_default": [C.POINTER(CgOpts)],
+    "apcg_cg_solve": [P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
+    "apcg_cg_plan_create": [P, P, C.POINTER(CgOpts), PP],
+    "apcg_cg_plan_solve": [P, P, P, C.POINTER(CgResult)],
+    "apcg_cg_plan_solve_async": [P, P, P],
+    "apcg_cg_plan_result": [P, C.POINTER(CgResult)],
+    "apcg_cg_plan_destroy": [P],
+    "apcg_cg_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
+    "apcg_cg_solve_host": [i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
+    "apcg_sim_create": [i32, PP],
+    "apcg_sim_op": [P, i32, i32, C.POINTER(u64), C.POINTER(i32)],
+    "apcg_sim_complete": [P, i32, u64],
+    "apcg_sim_log": [P, C.c_char_p, C.c_size_t],
+    "apcg_sim_destroy": [P],
+}
+_RESTYPE = {"apcg_last_error_string": C.c_char_p, "apcg_version": i32}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libapcg.so (raises ImportError when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"libapcg.so is not built ({p} missing); run the repository's build() first")
+        lib = C.CDLL(p)
+        for name, args in PROTOS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = _RESTYPE.get(name, S)
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().apcg_last_error_string().decode()
+
+
+def call(name: str, *args):
+    """Call an entry point; raise ApcgError on a non-zero status."""
+    st = getattr(load(), name)(*args)
+    if st != OK:
+        raise ApcgError(st, last_error())
+    return st
+
+
+# ---------------------------------------------------------------- handles and helpers
+
+
+def _out():
+    return C.c_void_p()
+
+
+def _ptr(t) -> int:
+    """Raw data pointer of a tensor (or an int pointer)."""
+    return t if isinstance(t, int) else int(t.data_ptr())
+
+
+def ctx_create(stream=None):
+    h = _out()
+    if stream is None:
+        call("apcg_ctx_create", C.byref(h))
+    else:
+        s = stream if isinstance(stream, int) else int(stream.cuda_stream)
+        call("apcg_ctx_create_from_stream", C.c_void_p(s), C.byref(h))
+    return h.value
+
+
+def ctx_get_stream(ctx) -> int:
+    s = _out()
+    call("apcg_ctx_get_stream", C.c_void_p(ctx), C.byref(s))
+    return s.value or 0
+
+
+def ctx_query_idle(ctx) -> bool:
+    v = i32()
+    call("apcg_ctx_query_idle", C.c_void_p(ctx), C.byref(v))
+    return bool(v.value)
+
+
+def ctx_fork(parent, n):
+    arr = (C.c_void_p * n)()
+    call("apcg_ctx_fork", C.c_void_p(parent), n, arr)
+    return [arr[i] for i in range(n)]
+
+
+def ctx_join(parent, children, mode=JOIN_DESTROY):
+    arr = (C.c_void_p * len(children))(*children)
+    call("apcg_ctx_join", C.c_void_p(parent), len(children), arr, mode)
+
+
+def register_memory(ptr, nbytes) -> int:
+    v = u64()
+    call("apcg_register_memory", C.c_void_p(_ptr(ptr)), nbytes, C.byref(v))
+    return v.value
+
+
+def scalar_create():
+    h = _out()
+    call("apcg_scalar_create", F64, C.byref(h))
+    return h.value
+
+
+def scalar_get(s) -> float:
+    v = f64()
+    call("apcg_scalar_get", C.c_void_p(s), C.byref(v))
+    return v.value
+
+
+def scalar_id(s) -> int:
+    v = u64()
+    call("apcg_scalar_id", C.c_void_p(s), C.byref(v))
+    return v.value
+
+
+def scalar_device_ptr(s) -> int:
+    v = _out()
+    call("apcg_scalar_device_ptr", C.c_void_p(s), C.byref(v))
+    return v.value
+
+
+def vec_wrap(t, dtype=None):
+    """View a contiguous 1-D CUDA tensor (float64 or float32) as an apcg_vec."""
+    import torch
+
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is None:
+        dtype = F64 if t.dtype == torch.float64 else F32 if t.dtype == torch.float32 else None
+        if dtype is None:
+            raise ValueError(f"unsupported dtype {t.dtype}")
+    h = _out()
+    call("apcg_vec_wrap", C.c_void_p(_ptr(t) if t.numel() else 0), t.numel(), dtype, C.byref(h))
+    return h.value
+
+
+def vec_id(v) -> int:
+    x = u64()
+    call("apcg_vec_id", C.c_void_p(v), C.byref(x))
+    return x.value
+
+
+def mat_wrap(rowptr, col, val, ncols=None):
+    """View CUDA tensors rowptr (int32), col (int32), val (float64/float32) as an apcg_mat."""
+    import torch
+
+    nrows = rowptr.numel() - 1
+    dtype = F64 if val.dtype == torch.float64 else F32
+    h = _out()
+    call(
+        "apcg_mat_csr_wrap",
+        C.c_void_p(_ptr(rowptr)),
+        C.c_void_p(_ptr(col) if col.numel() else 0),
+        C.c_void_p(_ptr(val) if val.numel() else 0),
+        nrows,
+        nrows if ncols is None else ncols,
+        col.numel(),
+        dtype,
+        C.byref(h),
+    )
+    return h.value
+
+
+def mat_id(A) -> int:
+    x = u64()
+    call("apcg_mat_id", C.c_void_p(A), C.byref(x))
+    return x.value
+
+
+def cg_opts(rtol=1e-8, atol=0.0, max_it=0, check_every=1, mode="auto", history_len=0):
+    o = CgOpts()
+    call("apcg_cg_opts_default", C.byref(o))
+    o.rtol, o.atol, o.max_it, o.check_every = rtol, atol, max_it, check_every
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    o.history_len = history_len
+    hist = None
+    if history_len:
+        hist = ((C.c_double * history_len)(), (C.c_double * history_len)())
+        o.alpha_hist = C.cast(hist[0], C.POINTER(C.c_double))
+        o.beta_hist = C.cast(hist[1], C.POINTER(C.c_double))
+    o._hist = hist  # keep the buffers alive with the struct
+    return o
+
+
+def cg_solve(ctx, A, b, x, opts: CgOpts) -> dict:
+    res = CgResult()
+    call("apcg_cg_solve", C.c_void_p(ctx), C.c_void_p(A), C.c_void_p(b), C.c_void_p(x), C.byref(opts), C.byref(res))
+    out = res.as_dict()
+    if opts.history_len:
+        out["alpha"] = list(opts._hist[0])
+        out["beta"] = list(opts._hist[1])
+    return out
+
+
+def cg_plan_create(ctx, A, opts: CgOpts):
+    h = _out()
+    call("apcg_cg_plan_create", C.c_void_p(ctx), C.c_void_p(A), C.byref(opts), C.byref(h))
+    return h.value
+
+
+def cg_plan_solve(plan, b, x) -> dict:
+    res = CgResult()
+    call("apcg_cg_plan_solve", C.c_void_p(plan), C.c_void_p(b), C.c_void_p(x), C.byref(res))
+    return res.as_dict()
+
+
+def cg_plan_profile(plan, b, x, iters: int) -> list[float]:
+    ms = (C.c_float * 3)()
+    call("apcg_cg_plan_profile", C.c_void_p(plan), C.c_void_p(b), C.c_void_p(x), iters, ms)
+    return [float(v) for v in ms]
+
+
+def cg_solve_host(rowptr, col, val, b, x, opts: CgOpts) -> dict:
+    """Solve with numpy arrays in host memory (x is updated in place)."""
+    import numpy as np
+
+    for a, dt in ((rowptr, np.int32), (col, np.int32), (val, np.float64), (b, np.float64), (x, np.float64)):
+        if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous int32/float64")
+    res = CgResult()
+    call(
+        "apcg_cg_solve_host",
+        rowptr.shape[0] - 1,
+        col.shape[0],
+        rowptr.ctypes.data_as(P),
+        col.ctypes.data_as(P),
+        val.ctypes.data_as(P),
+        b.ctypes.data_as(P),
+        x.ctypes.data_as(P),
+        C.byref(opts),
+        C.byref(res),
+    )
+    return res.as_dict()
+
+
+def get_counters() -> dict:
+    c = Counters()
+    call("apcg_get_counters", C.byref(c))
+    return c.as_dict()
+
+
+def reset_counters():
+    call("apcg_reset_counters")
+
+
+def header_functions() -> list[str]:
+    """Entry points declared in include/apcg.h."""
+    import re
+
+    txt = open(HEADER).read()
+    return re.findall(r"^APCG_API\s+[\w\s\*]+?\b(apcg_\w+)\s*\(", txt, flags=re.M)
+
+
+# ---------------------------------------------------------------- host-only marking simulator
+
+
+class Sim:
+    """The host-only simulator of the marking rules (apcg_sim_*)."""
+
+    def __init__(self, nctx: int):
+        h = _out()
+        call("apcg_sim_create", nctx, C.byref(h))
+        self.h = h.value
+
+    def op(self, ctx: int, accesses):
+        ids = (u64 * len(accesses))(*[a[0] for a in accesses])
+        modes = (i32 * len(accesses))(*[a[1] for a in accesses])
+        call("apcg_sim_op", C.c_void_p(self.h), ctx, len(accesses), ids, modes)
+
+    def complete(self, ctx: int, seq: int):
+        call("apcg_sim_complete", C.c_void_p(self.h), ctx, seq)
+
+    def log(self) -> list[str]:
+        buf = C.create_string_buffer(1 << 16)
+        call("apcg_sim_log", C.c_void_p(self.h), buf, len(buf))
+        return [l for l in buf.value.decode().split("\n") if l]
+
+    def close(self):
+        if self.h:
+            call("apcg_sim_destroy", C.c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

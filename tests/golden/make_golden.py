@@ -42,6 +42,16 @@ def main():
         "beta": [float(v).hex() for v in r["beta"]],
         "rr_final": float(r["rr"]).hex(),
     }
+    p = single_problem("c2", seed=0)
+    r = oracle.pcg(p.A, p.b, rtol=1e-8, check_every=10, hist_len=10)
+    out["c2_full_seed0"] = {
+        "workload": "3-D 7-point Laplacian 128^3, x_true ~ U[-1,1] seed 0, b = A x_true, x0 = 0, rtol 1e-8, k = 10",
+        "iters": r["iters"],
+        "reason": r["reason"],
+        "alpha": [float(v).hex() for v in r["alpha"]],
+        "beta": [float(v).hex() for v in r["beta"]],
+        "rr_final": float(r["rr"]).hex(),
+    }
     with open(os.path.join(HERE, "oracle_pcg_history.json"), "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
         f.write("\n")
