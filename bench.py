@@ -432,6 +432,7 @@ def main():
     ap.add_argument("--impl", choices=["apcg", "reference"], default="apcg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true", help="only the set-up and 3 iterations, kernels launched one by one (for profilers)")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
@@ -448,7 +449,35 @@ def main():
 
         while not _build.up_to_date() and time.time() < deadline:
             time.sleep(1)
+    if args.ncu_case:
+        ncu_case()
+        return
     run_apcg(args, rank, world, local)
+
+
+def ncu_case():
+    """Set-up kernel plus 3 iterations of the benchmark workload, each kernel launched on its own."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+    from synthetic import single_problem
+
+    dev = torch.device("cuda", 0)
+    apcg.load()
+    p = single_problem("c2", seed=0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rowptr, col, val, b = t(p.A.rowptr), t(p.A.col), t(p.A.val), t(p.b)
+    x = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    ctx = apcg.ctx_create()
+    A = apcg.mat_wrap(rowptr, col, val)
+    vb, vx = apcg.vec_wrap(b), apcg.vec_wrap(x)
+    plan = apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=RTOL, check_every=K_CHECK, mode="async", max_it=MAX_IT))
+    ms = apcg.cg_plan_profile(plan, vb, vx, 3)
+    apcg.call("apcg_cg_plan_destroy", C.c_void_p(plan))
+    print(json.dumps({"ncu_case": "c2 setup + 3 iterations", "kernel_ms": ms}))
 
 
 if __name__ == "__main__":

@@ -334,9 +334,9 @@ APCG_API apcg_status apcg_cg_opts_default(apcg_cg_opts* opts);
 typedef struct {
   int32_t iters;            /* completed iterations */
   int32_t reason;           /* apcg_reason */
-  double rr;                /* (r,r) of the recursively updated residual at exit */
+  double rr;                /* (r,r) of the recursively updated residual at the last convergence test */
   double bnorm;             /* ||b||_2 */
-  double rel_res;           /* sqrt(rr) / bnorm (sqrt(rr) when b = 0) */
+  double rel_res;           /* sqrt(rr) / bnorm (sqrt(rr) when b = 0), at the last convergence test */
   int64_t kernel_launches;  /* kernels this solve executed on the device */
 } apcg_cg_result;
 

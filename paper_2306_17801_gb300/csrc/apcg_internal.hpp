@@ -115,6 +115,11 @@ class OpScope {
   OpScope& read(apcg_id id) { return add(id, kRead); }
   OpScope& write(apcg_id id) { return add(id, kWrite); }
   OpScope& rw(apcg_id id) { return add(id, kReadWrite); }
+  // The launch may raise a device-side error flag (checked by a global-blocking finish).
+  OpScope& may_flag_errors() {
+    flags_errors_ = true;
+    return *this;
+  }
   apcg_status begin();
   apcg_status finish();
 
@@ -129,6 +134,7 @@ class OpScope {
   };
   apcg_ctx ctx_;
   std::vector<Item> ids_;
+  bool flags_errors_ = false;
 };
 
 apcg_status ensure_scratch(apcg_ctx ctx);

@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "apcg_internal.hpp"
@@ -53,6 +54,7 @@ struct CgArgs {
   double* r;
   double* p;
   double* w;
+  double* z;
   CgState* st;
   double* partials;
   double* alpha_h;
@@ -69,8 +71,8 @@ __global__ void __launch_bounds__(kThreads) cg_setup_kernel(CgArgs a, const doub
   __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
   __shared__ double red[3 * 32];
   double v[3] = {0.0, 0.0, 0.0};
-  dev::spmv_warp_tiles<U, double>(a.rowptr, a.col, a.val, a.x, a.n, sm[threadIdx.x >> 5].buf,
-                                  [&](int32_t i, double ax) {
+  dev::spmv_warp_tiles<U, false, double>(a.rowptr, a.col, a.val, a.x, a.n, sm[threadIdx.x >> 5].buf,
+                                         [&](int32_t i, double ax, double) {
                                     const double bi = __ldg(b + i);
                                     const double ri = bi - ax;
                                     const double zi = __ldg(a.dinv + i) * ri;
@@ -105,11 +107,11 @@ __global__ void __launch_bounds__(kThreads) cg_spmv_dot_kernel(CgArgs a) {
   __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
   __shared__ double red[32];
   double v[1] = {0.0};
-  dev::spmv_warp_tiles<U, double>(a.rowptr, a.col, a.val, a.p, a.n, sm[threadIdx.x >> 5].buf,
-                                  [&](int32_t i, double s) {
-                                    a.w[i] = s;
-                                    v[0] += __ldg(a.p + i) * s;
-                                  });
+  dev::spmv_warp_tiles<U, true, double>(a.rowptr, a.col, a.val, a.p, a.n, sm[threadIdx.x >> 5].buf,
+                                        [&](int32_t i, double s, double p_i) {
+                                          a.w[i] = s;
+                                          v[0] += p_i * s;
+                                        });
   double tot[1];
   if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
     CgState* st = a.st;
@@ -127,10 +129,16 @@ __global__ void __launch_bounds__(kThreads) cg_spmv_dot_kernel(CgArgs a) {
   }
 }
 
-// K2: x += alpha p; r -= alpha w; z = D^-1 r; rho' = (r,z); rr = (r,r); test; beta.
+// K2: x += alpha p; r -= alpha w; z = D^-1 r (stored for K3); rho' = (r,z);
+// on convergence-test iterations also rr = (r,r); then the test and beta.
+// The test runs when the iteration count is a multiple of k or reaches max_it,
+// decided from the state block at kernel entry, so the same kernel serves
+// every position of a captured block.  Without the test the kernel spends
+// four float64 operations per row (the float64 pipe is GB300's scarcest
+// resource here); (r,r) adds a fifth only when it is needed.
 template <bool HOST>
-__global__ void __launch_bounds__(kThreads) cg_update_kernel(CgArgs a, double alpha_host,
-                                                             cudaGraphConditionalHandle cond, int32_t use_cond) {
+__global__ void __launch_bounds__(kThreads, 4) cg_update_kernel(CgArgs a, double alpha_host,
+                                                                cudaGraphConditionalHandle cond, int32_t use_cond) {
   if (!HOST && read_done(a.st)) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
       a.st->body_runs += 1;
@@ -139,53 +147,90 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(CgArgs a, double al
     return;
   }
   const double alpha = HOST ? alpha_host : a.st->alpha;
+  bool check = true;
+  if (!HOST) {
+    const int32_t it = a.st->iter + 1;
+    check = (it % a.st->check_every == 0) || it >= a.st->max_it;
+  }
   __shared__ double red[2 * 32];
   double v[2] = {0.0, 0.0};
   const int64_t n = a.n, np = n >> 1, stride = (int64_t)gridDim.x * blockDim.x;
   double2* x2 = reinterpret_cast<double2*>(a.x);
   double2* r2 = reinterpret_cast<double2*>(a.r);
+  double2* z2 = reinterpret_cast<double2*>(a.z);
   const double2* p2 = reinterpret_cast<const double2*>(a.p);
   const double2* w2 = reinterpret_cast<const double2*>(a.w);
   const double2* d2 = reinterpret_cast<const double2*>(a.dinv);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
-    double2 xx = x2[i], rr = r2[i];
-    const double2 pp = __ldg(p2 + i), ww = dev::ld_stream2(w2 + i), dd = __ldg(d2 + i);
-    xx.x += alpha * pp.x;
-    xx.y += alpha * pp.y;
-    rr.x -= alpha * ww.x;
-    rr.y -= alpha * ww.y;
-    x2[i] = xx;
-    r2[i] = rr;
-    v[0] += rr.x * (dd.x * rr.x);
-    v[0] += rr.y * (dd.y * rr.y);
-    v[1] += rr.x * rr.x;
-    v[1] += rr.y * rr.y;
-  }
+  constexpr int V = 2;  // double2 pairs in flight per thread and array
+  auto sweep = [&](auto with_rr) {
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < np; i0 += V * stride) {
+      double2 xx[V], rr[V], pp[V], ww[V], dd[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < np) {
+          xx[u] = x2[i];
+          rr[u] = r2[i];
+          pp[u] = __ldg(p2 + i);
+          ww[u] = dev::ld_stream2(w2 + i);
+          dd[u] = __ldg(d2 + i);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < np) {
+          xx[u].x = fma(alpha, pp[u].x, xx[u].x);
+          xx[u].y = fma(alpha, pp[u].y, xx[u].y);
+          rr[u].x = fma(-alpha, ww[u].x, rr[u].x);
+          rr[u].y = fma(-alpha, ww[u].y, rr[u].y);
+          const double2 zz = make_double2(dd[u].x * rr[u].x, dd[u].y * rr[u].y);
+          x2[i] = xx[u];
+          r2[i] = rr[u];
+          z2[i] = zz;
+          v[0] = fma(rr[u].x, zz.x, v[0]);
+          v[0] = fma(rr[u].y, zz.y, v[0]);
+          if (decltype(with_rr)::value) {
+            v[1] = fma(rr[u].x, rr[u].x, v[1]);
+            v[1] = fma(rr[u].y, rr[u].y, v[1]);
+          }
+        }
+      }
+    }
+  };
+  if (check)
+    sweep(std::true_type{});
+  else
+    sweep(std::false_type{});
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t i = n - 1;
-    a.x[i] += alpha * a.p[i];
-    const double ri = a.r[i] - alpha * a.w[i];
+    a.x[i] = fma(alpha, a.p[i], a.x[i]);
+    const double ri = fma(-alpha, a.w[i], a.r[i]);
+    const double zi = a.dinv[i] * ri;
     a.r[i] = ri;
-    v[0] += ri * (a.dinv[i] * ri);
-    v[1] += ri * ri;
+    a.z[i] = zi;
+    v[0] = fma(ri, zi, v[0]);
+    if (check) v[1] = fma(ri, ri, v[1]);
   }
   double tot[2];
   if (dev::grid_sum_last<2>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
     CgState* st = a.st;
     const double rz = tot[0], rr = tot[1];
     st->rho_new = rz;
-    st->rr = rr;
+    if (check) st->rr = rr;
     if (!HOST) {
       const int32_t it = st->iter + 1;
       st->iter = it;
       int32_t done = 0;
-      if (rr == 0.0)
+      // An exactly zero residual ends the solve at any iteration; between
+      // tests (r, D^-1 r) = 0 stands for r = 0 (D^-1 is positive).
+      if ((check && rr == 0.0) || rz == 0.0)
         done = kDoneConverged;
-      else if ((it % st->check_every == 0 || it == st->max_it) && sqrt(rr) <= st->tol)
+      else if (check && sqrt(rr) <= st->tol)
         done = kDoneConverged;
       else if (it >= st->max_it)
         done = kDoneNotConverged;
-      else if (!isfinite(rr))
+      else if (!isfinite(rz) || (check && !isfinite(rr)))
         done = kDoneBreakdown;
       if (!done) {
         const double beta = rz / st->rho;
@@ -202,25 +247,38 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(CgArgs a, double al
   }
 }
 
-// K3: p = D^-1 r + beta p.
+// K3: p = z + beta p (one fused multiply-add per row).
 template <bool HOST>
-__global__ void __launch_bounds__(kThreads) cg_aypx_kernel(CgArgs a, double beta_host) {
+__global__ void __launch_bounds__(kThreads, 4) cg_aypx_kernel(CgArgs a, double beta_host) {
   if (!HOST && read_done(a.st)) return;
   const double beta = HOST ? beta_host : a.st->beta;
   const int64_t n = a.n, np = n >> 1, stride = (int64_t)gridDim.x * blockDim.x;
   double2* p2 = reinterpret_cast<double2*>(a.p);
-  const double2* r2 = reinterpret_cast<const double2*>(a.r);
-  const double2* d2 = reinterpret_cast<const double2*>(a.dinv);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
-    double2 pp = p2[i];
-    const double2 rr = __ldg(r2 + i), dd = __ldg(d2 + i);
-    pp.x = dd.x * rr.x + beta * pp.x;
-    pp.y = dd.y * rr.y + beta * pp.y;
-    p2[i] = pp;
+  const double2* z2 = reinterpret_cast<const double2*>(a.z);
+  constexpr int V = 4;  // double2 pairs in flight per thread and array
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < np; i0 += V * stride) {
+    double2 pp[V], zz[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < np) {
+        pp[u] = p2[i];
+        zz[u] = dev::ld_stream2(z2 + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < np) {
+        pp[u].x = fma(beta, pp[u].x, zz[u].x);
+        pp[u].y = fma(beta, pp[u].y, zz[u].y);
+        p2[i] = pp[u];
+      }
+    }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t i = n - 1;
-    a.p[i] = a.dinv[i] * a.r[i] + beta * a.p[i];
+    a.p[i] = fma(beta, a.p[i], a.z[i]);
   }
 }
 
@@ -255,6 +313,7 @@ CgArgs make_args(apcg_cg_plan P, double* x) {
   a.r = P->r;
   a.p = P->p;
   a.w = P->w;
+  a.z = P->z;
   a.st = P->st;
   a.partials = P->partials;
   a.alpha_h = P->alpha_h;
@@ -513,13 +572,13 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   void* k1 = P->u == 4 ? (void*)cg_spmv_dot_kernel<4, false> : P->u == 6 ? (void*)cg_spmv_dot_kernel<6, false> : (void*)cg_spmv_dot_kernel<8, false>;
   P->grid_spmv = occupancy_grid(k1, sms, spmv_blocks);
   P->grid_vec = occupancy_grid((void*)cg_update_kernel<false>, sms, vec_blocks);
-  // Workspace: dinv, r, p, w, partials, state, histories (one stream-ordered block).
+  // Workspace: dinv, r, p, w, z, partials, state, histories (one stream-ordered block).
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(double) * (size_t)(P->n > 0 ? P->n : 1));
   const size_t npart = up(sizeof(double) * dev::kMaxPartials * 3);
   const size_t nst = up(sizeof(CgState));
   const size_t nh = up(sizeof(double) * (size_t)(P->hist_len > 0 ? P->hist_len : 1));
-  const size_t total = 4 * nv + npart + nst + 2 * nh;
+  const size_t total = 5 * nv + npart + nst + 2 * nh;
   char* ws = nullptr;
   APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
   P->ws = ws;
@@ -527,11 +586,12 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   P->r = reinterpret_cast<double*>(ws + nv);
   P->p = reinterpret_cast<double*>(ws + 2 * nv);
   P->w = reinterpret_cast<double*>(ws + 3 * nv);
-  P->partials = reinterpret_cast<double*>(ws + 4 * nv);
-  P->st = reinterpret_cast<CgState*>(ws + 4 * nv + npart);
-  P->alpha_h = reinterpret_cast<double*>(ws + 4 * nv + npart + nst);
-  P->beta_h = reinterpret_cast<double*>(ws + 4 * nv + npart + nst + nh);
-  APCG_CUDA(cudaMemsetAsync(ws + 4 * nv, 0, npart + nst + 2 * nh, ctx->stream));
+  P->z = reinterpret_cast<double*>(ws + 4 * nv);
+  P->partials = reinterpret_cast<double*>(ws + 5 * nv);
+  P->st = reinterpret_cast<CgState*>(ws + 5 * nv + npart);
+  P->alpha_h = reinterpret_cast<double*>(ws + 5 * nv + npart + nst);
+  P->beta_h = reinterpret_cast<double*>(ws + 5 * nv + npart + nst + nh);
+  APCG_CUDA(cudaMemsetAsync(ws + 5 * nv, 0, npart + nst + 2 * nh, ctx->stream));
   APCG_CUDA(cudaMallocHost((void**)&P->st_host, sizeof(CgState)));
   APCG_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   {

@@ -51,7 +51,7 @@ struct apcg_cg_plan_s {
   int32_t n = 0, k = 1, max_it = 0, hist_len = 0, mode = APCG_MODE_ASYNC_GRAPH, u = 8;
   int grid_spmv = 1, grid_vec = 1;
   char* ws = nullptr;    // workspace block (stream-ordered allocation)
-  double *dinv = nullptr, *r = nullptr, *p = nullptr, *w = nullptr, *partials = nullptr;
+  double *dinv = nullptr, *r = nullptr, *p = nullptr, *w = nullptr, *z = nullptr, *partials = nullptr;
   double *alpha_h = nullptr, *beta_h = nullptr;
   apcg::CgState* st = nullptr;       // device
   apcg::CgState* st_host = nullptr;  // pinned mirror

@@ -239,7 +239,7 @@ apcg_status OpScope::finish() {
   if (ctx_->type == APCG_STREAM_GLOBAL_BLOCKING) {
     APCG_CUDA(cudaStreamSynchronize(ctx_->stream));
     counters().host_syncs++;
-    return ctx_check_device_error(ctx_);
+    if (flags_errors_) return ctx_check_device_error(ctx_);
   }
   return APCG_OK;
 }

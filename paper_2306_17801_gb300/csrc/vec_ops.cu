@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(kVecThreads) pmult_kernel(int64_t n, double* _
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) w[n - 1] = x[n - 1] * y[n - 1];
 }
 
-// y := A x; with `out`, also out := x'y (A square).
-template <int U>
+// y := A x; with DOT, also out := x'y (A square).
+template <int U, bool DOT>
 __global__ void __launch_bounds__(kSpmvThreads) spmv_kernel(const int32_t* __restrict__ rowptr,
                                                             const int32_t* __restrict__ col,
                                                             const double* __restrict__ val, int32_t nrows,
@@ -132,11 +132,12 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_kernel(const int32_t* __res
   __shared__ dev::SpmvSmem<U, double> sm[kSpmvThreads / 32];
   __shared__ double red[32];
   double v[1] = {0.0};
-  dev::spmv_warp_tiles<U, double>(rowptr, col, val, x, nrows, sm[threadIdx.x >> 5].buf, [&](int32_t row, double s) {
-    y[row] = s;
-    if (out) v[0] += __ldg(x + row) * s;
-  });
-  if (!out) return;
+  dev::spmv_warp_tiles<U, DOT, double>(rowptr, col, val, x, nrows, sm[threadIdx.x >> 5].buf,
+                                       [&](int32_t row, double s, double x_row) {
+                                         y[row] = s;
+                                         if (DOT) v[0] += x_row * s;
+                                       });
+  if (!DOT) return;
   double tot[1];
   if (dev::grid_sum_last<1>(v, partials, ticket, red, tot) && threadIdx.x == 0) *out = tot[0];
 }
@@ -440,9 +441,11 @@ static apcg_status mat_mult_impl(apcg_ctx ctx_in, apcg_mat A, apcg_vec x, apcg_v
   const int64_t lim = (int64_t)ctx_num_sms(ctx) * 8;
   if (g > lim) g = lim;
   if (g < 1) g = 1;
-  spmv_kernel<kSpmvU><<<(int)g, kSpmvThreads, 0, ctx->stream>>>(
-      A->rowptr, A->col, static_cast<const double*>(A->val), A->nrows, static_cast<const double*>(x->dptr),
-      static_cast<double*>(y->dptr), out ? out->dptr : nullptr, ctx->scratch.partials, ctx->scratch.ticket);
+  auto kern = out ? spmv_kernel<kSpmvU, true> : spmv_kernel<kSpmvU, false>;
+  kern<<<(int)g, kSpmvThreads, 0, ctx->stream>>>(A->rowptr, A->col, static_cast<const double*>(A->val), A->nrows,
+                                                 static_cast<const double*>(x->dptr), static_cast<double*>(y->dptr),
+                                                 out ? out->dptr : nullptr, ctx->scratch.partials,
+                                                 ctx->scratch.ticket);
   APCG_CUDA(cudaGetLastError());
   count_kernels(1);
   return op.finish();
@@ -466,7 +469,7 @@ apcg_status apcg_pc_jacobi_setup_async(apcg_ctx ctx_in, apcg_mat A, apcg_vec din
   apcg_ctx ctx;
   APCG_TRY(resolve_ctx(ctx_in, &ctx));
   OpScope op(ctx);
-  op.read(A->id).write(dinv->id);
+  op.read(A->id).write(dinv->id).may_flag_errors();
   APCG_TRY(op.begin());
   APCG_TRY(launch_jacobi_setup(ctx, A, static_cast<double*>(dinv->dptr)));
   return op.finish();
