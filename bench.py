@@ -274,7 +274,7 @@ def run_apcg(args, rank, world, local):
         ms_k = apcg.cg_plan_profile(prof_plan, vb, vx, 30)
         apcg.call("apcg_cg_plan_destroy", V(prof_plan))
         bytes_k1 = 12 * nnz + 4 * (n + 1) + 16 * n
-        bytes_k2, bytes_k3 = 56 * n, 32 * n
+        bytes_k2, bytes_k3 = 64 * n, 24 * n  # K2: read x,r,p,w,dinv write x,r,z; K3: read p,z write p
         bytes_iter = 12 * nnz + 4 * (n + 1) + 104 * n
         peak, peak_kind = _peaks()
         ach = bytes_k1 / (ms_k[0] * 1e-3) / 1e9
@@ -405,7 +405,7 @@ def small_case(apcg, ctx, dev):
     A = apcg.mat_wrap(rowptr, col, val)
     vb, vx = apcg.vec_wrap(b), apcg.vec_wrap(x)
     out = {"workload": "2D 5-point Laplacian 64^2 (n=4096, nnz=20,224), rtol 1e-8, k=1"}
-    for mode in ("host_sync", "async", "async_graph"):
+    for mode in ("host_sync", "async", "async_graph", "persistent"):
         pl = apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=1e-8, check_every=1, mode=mode))
         best = None
         for _ in range(5):
@@ -418,6 +418,7 @@ def small_case(apcg, ctx, dev):
         out[mode] = {"us_per_iteration": 1e6 * best / r["iters"], "iters": r["iters"], "ms_per_solve": 1e3 * best}
         apcg.call("apcg_cg_plan_destroy", V(pl))
     out["speedup_async_graph_vs_host_sync"] = out["host_sync"]["us_per_iteration"] / out["async_graph"]["us_per_iteration"]
+    out["speedup_persistent_vs_host_sync"] = out["host_sync"]["us_per_iteration"] / out["persistent"]["us_per_iteration"]
     for h in (vb, vx):
         apcg.call("apcg_vec_destroy", V(h))
     apcg.call("apcg_mat_destroy", V(A))

@@ -315,7 +315,12 @@ typedef enum {
   APCG_MODE_AUTO = 4
 } apcg_mode;
 
-typedef enum { APCG_CONVERGED = 0, APCG_NOT_CONVERGED = 1, APCG_BREAKDOWN = 2 } apcg_reason;
+typedef enum {
+  APCG_CONVERGED = 0,
+  APCG_NOT_CONVERGED = 1,
+  APCG_BREAKDOWN = 2,
+  APCG_BAD_DIAGONAL = 3 /* batched solves: this system has a zero, missing or non-finite diagonal entry */
+} apcg_reason;
 
 typedef struct {
   double rtol;          /* stop when ||r||_2 <= max(rtol * ||b||_2, atol) */
@@ -390,6 +395,58 @@ APCG_API apcg_status apcg_cg_plan_profile(apcg_cg_plan plan, apcg_vec b, apcg_ve
  */
 APCG_API apcg_status apcg_cg_solve_host(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const double* val,
                                const double* b, double* x, const apcg_cg_opts* opts, apcg_cg_result* res);
+
+/* ------------------------------------------------------------------ batched solves (many independent systems) */
+
+/*
+ * Many independent SPD systems solved together by Jacobi-PCG (the paper's
+ * method applied to each system; batching itself is not in the paper).  The
+ * systems are concatenated row-wise: system s owns rows sys_row_off[s] ..
+ * sys_row_off[s+1]-1; rowptr (device, int32 [N+1], N = sys_row_off[nsys])
+ * holds nnz positions over the whole concatenation; col (device, int32) holds
+ * column indices local to each system (0 .. n_s-1); val (device, float64).
+ * b and x are concatenated the same way (device, float64 [N]; x holds x0 on
+ * entry).  Each system must have at most 65536 rows.
+ *
+ * Every system is solved by one thread-block cluster that runs the whole
+ * solve in one launch with a per-system convergence test; clusters take
+ * systems longest first from a device work queue.  Systems are grouped into
+ * size classes (powers of two in n), and each class has a launch shape
+ * (CTAs per cluster, threads per CTA, rows per thread) picked by the built-in
+ * table or by apcg_batch_plan_tune.  All class launches of a solve form one
+ * CUDA graph whose branches run concurrently.
+ *
+ * opts: rtol, atol, max_it (per system; <= 0 selects 10 n_s), check_every;
+ * mode and history are ignored.  sys_row_off is host memory; it is copied.
+ */
+typedef struct apcg_batch_plan_s* apcg_batch_plan;
+
+typedef struct {
+  int32_t iters;   /* completed iterations of this system */
+  int32_t reason;  /* apcg_reason */
+  double rel_res;  /* ||r|| / ||b|| at the last convergence test (recursive residual) */
+} apcg_batch_result;
+
+APCG_API apcg_status apcg_batch_plan_create(apcg_ctx ctx, int32_t nsys, const int32_t* sys_row_off,
+                                            const int32_t* rowptr, const int32_t* col, const double* val,
+                                            const apcg_cg_opts* opts, apcg_batch_plan* out);
+/* Solve all systems; results (host [nsys]) may be NULL.  Blocks until done when results != NULL. */
+APCG_API apcg_status apcg_batch_plan_solve(apcg_batch_plan plan, const double* b, double* x,
+                                           apcg_batch_result* results);
+/*
+ * Autotuner: for every size class, time each candidate launch shape on the
+ * class's own systems (b given, x0 = 0, a private x) and keep the fastest.
+ * Writes up to `cap` lines "n_lo n_hi C threads rows_per_thread ms" into
+ * `table` (may be NULL).  Blocks until done.
+ */
+APCG_API apcg_status apcg_batch_plan_tune(apcg_batch_plan plan, const double* b, char* table, size_t cap);
+APCG_API apcg_status apcg_batch_plan_destroy(apcg_batch_plan plan);
+
+/* One-shot form of create + solve + destroy. */
+APCG_API apcg_status apcg_cg_solve_batched(apcg_ctx ctx, int32_t nsys, const int32_t* sys_row_off,
+                                           const int32_t* rowptr, const int32_t* col, const double* val,
+                                           const double* b, double* x, const apcg_cg_opts* opts,
+                                           apcg_batch_result* results);
 
 /* ------------------------------------------------------------------ host-only simulation of the marking rules */
 

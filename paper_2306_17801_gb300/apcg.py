@@ -98,6 +98,12 @@ class CgResult(C.Structure):
         }
 
 
+class BatchResult(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rel_res", C.c_double)]
+
+
+REASONS[3] = "bad_diagonal"
+
 P = C.c_void_p
 PP = C.POINTER(C.c_void_p)
 S = C.c_int32
@@ -166,6 +172,11 @@ PROTOS = {
     "apcg_cg_plan_destroy": [P],
     "apcg_cg_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
     "apcg_cg_solve_host": [i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
+    "apcg_batch_plan_create": [P, i32, P, P, P, P, C.POINTER(CgOpts), PP],
+    "apcg_batch_plan_solve": [P, P, P, P],
+    "apcg_batch_plan_tune": [P, P, C.c_char_p, C.c_size_t],
+    "apcg_batch_plan_destroy": [P],
+    "apcg_cg_solve_batched": [P, i32, P, P, P, P, P, P, C.POINTER(CgOpts), P],
     "apcg_sim_create": [i32, PP],
     "apcg_sim_op": [P, i32, i32, C.POINTER(u64), C.POINTER(i32)],
     "apcg_sim_complete": [P, i32, u64],
@@ -395,6 +406,39 @@ def cg_solve_host(rowptr, col, val, b, x, opts: CgOpts) -> dict:
         C.byref(res),
     )
     return res.as_dict()
+
+
+def batch_plan_create(ctx, sys_row_off, rowptr, col, val, opts: CgOpts):
+    """sys_row_off: host int32 array [nsys+1]; rowptr/col/val: CUDA tensors of the concatenation."""
+    import numpy as np
+
+    off = np.ascontiguousarray(sys_row_off, dtype=np.int32)
+    h = _out()
+    call(
+        "apcg_batch_plan_create", C.c_void_p(ctx), off.shape[0] - 1, off.ctypes.data_as(P), C.c_void_p(_ptr(rowptr)),
+        C.c_void_p(_ptr(col)), C.c_void_p(_ptr(val)), C.byref(opts), C.byref(h),
+    )
+    return h.value
+
+
+def batch_plan_solve(plan, b, x, nsys: int | None = None):
+    """Solve all systems; returns per-system results when nsys is given (blocks), else None (enqueued only)."""
+    if nsys is None:
+        call("apcg_batch_plan_solve", C.c_void_p(plan), C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x)), None)
+        return None
+    res = (BatchResult * nsys)()
+    call("apcg_batch_plan_solve", C.c_void_p(plan), C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x)), res)
+    return [{"iters": int(r.iters), "reason": REASONS.get(int(r.reason), int(r.reason)), "rel_res": float(r.rel_res)} for r in res]
+
+
+def batch_plan_tune(plan, b) -> list[tuple]:
+    buf = C.create_string_buffer(1 << 14)
+    call("apcg_batch_plan_tune", C.c_void_p(plan), C.c_void_p(_ptr(b)), buf, len(buf))
+    rows = []
+    for line in buf.value.decode().splitlines():
+        f = line.split()
+        rows.append({"n_lo": int(f[0]), "n_hi": int(f[1]), "cluster": int(f[2]), "threads": int(f[3]), "rows_per_thread": int(f[4]), "ms": float(f[5])})
+    return rows
 
 
 def get_counters() -> dict:

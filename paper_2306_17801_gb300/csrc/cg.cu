@@ -41,6 +41,9 @@ namespace apcg {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPersistentMaxRows = 65536;  // one cluster of 16 CTAs x 512 threads x 8 rows
+constexpr int kUpdV = 2;   // double2 pairs per thread in the update kernel
+constexpr int kAypxV = 2;  // double2 pairs per thread in the search-direction kernel
 
 // ------------------------------------------------------------------ kernels
 
@@ -106,10 +109,11 @@ __global__ void __launch_bounds__(kThreads) cg_spmv_dot_kernel(CgArgs a) {
   if (!HOST && read_done(a.st)) return;
   __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
   __shared__ double red[32];
+  const uint64_t keep = dev::policy_evict_last();
   double v[1] = {0.0};
   dev::spmv_warp_tiles<U, true, double>(a.rowptr, a.col, a.val, a.p, a.n, sm[threadIdx.x >> 5].buf,
                                         [&](int32_t i, double s, double p_i) {
-                                          a.w[i] = s;
+                                          dev::st_hint(a.w + i, s, keep);
                                           v[0] += p_i * s;
                                         });
   double tot[1];
@@ -161,7 +165,8 @@ __global__ void __launch_bounds__(kThreads, 4) cg_update_kernel(CgArgs a, double
   const double2* p2 = reinterpret_cast<const double2*>(a.p);
   const double2* w2 = reinterpret_cast<const double2*>(a.w);
   const double2* d2 = reinterpret_cast<const double2*>(a.dinv);
-  constexpr int V = 2;  // double2 pairs in flight per thread and array
+  constexpr int V = kUpdV;  // double2 pairs in flight per thread and array
+  const uint64_t keep = dev::policy_evict_last();
   auto sweep = [&](auto with_rr) {
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < np; i0 += V * stride) {
       double2 xx[V], rr[V], pp[V], ww[V], dd[V];
@@ -169,11 +174,11 @@ __global__ void __launch_bounds__(kThreads, 4) cg_update_kernel(CgArgs a, double
       for (int u = 0; u < V; ++u) {
         const int64_t i = i0 + u * stride;
         if (i < np) {
-          xx[u] = x2[i];
-          rr[u] = r2[i];
-          pp[u] = __ldg(p2 + i);
-          ww[u] = dev::ld_stream2(w2 + i);
-          dd[u] = __ldg(d2 + i);
+          xx[u] = dev::ld2_hint(x2 + i, keep);
+          rr[u] = dev::ld2_hint(r2 + i, keep);
+          pp[u] = dev::ld2_nc_hint(p2 + i, keep);
+          ww[u] = dev::ld2_nc_hint(w2 + i, keep);
+          dd[u] = dev::ld2_nc_hint(d2 + i, keep);
         }
       }
 #pragma unroll
@@ -185,9 +190,9 @@ __global__ void __launch_bounds__(kThreads, 4) cg_update_kernel(CgArgs a, double
           rr[u].x = fma(-alpha, ww[u].x, rr[u].x);
           rr[u].y = fma(-alpha, ww[u].y, rr[u].y);
           const double2 zz = make_double2(dd[u].x * rr[u].x, dd[u].y * rr[u].y);
-          x2[i] = xx[u];
-          r2[i] = rr[u];
-          z2[i] = zz;
+          dev::st2_hint(x2 + i, xx[u], keep);
+          dev::st2_hint(r2 + i, rr[u], keep);
+          dev::st2_hint(z2 + i, zz, keep);
           v[0] = fma(rr[u].x, zz.x, v[0]);
           v[0] = fma(rr[u].y, zz.y, v[0]);
           if (decltype(with_rr)::value) {
@@ -255,15 +260,16 @@ __global__ void __launch_bounds__(kThreads, 4) cg_aypx_kernel(CgArgs a, double b
   const int64_t n = a.n, np = n >> 1, stride = (int64_t)gridDim.x * blockDim.x;
   double2* p2 = reinterpret_cast<double2*>(a.p);
   const double2* z2 = reinterpret_cast<const double2*>(a.z);
-  constexpr int V = 4;  // double2 pairs in flight per thread and array
+  constexpr int V = kAypxV;  // double2 pairs in flight per thread and array
+  const uint64_t keep = dev::policy_evict_last();
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < np; i0 += V * stride) {
     double2 pp[V], zz[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       const int64_t i = i0 + u * stride;
       if (i < np) {
-        pp[u] = p2[i];
-        zz[u] = dev::ld_stream2(z2 + i);
+        pp[u] = dev::ld2_hint(p2 + i, keep);
+        zz[u] = dev::ld2_nc_hint(z2 + i, keep);
       }
     }
 #pragma unroll
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_aypx_kernel(CgArgs a, double b
       if (i < np) {
         pp[u].x = fma(beta, pp[u].x, zz[u].x);
         pp[u].y = fma(beta, pp[u].y, zz[u].y);
-        p2[i] = pp[u];
+        dev::st2_hint(p2 + i, pp[u], keep);
       }
     }
   }
@@ -512,6 +518,38 @@ apcg_status enqueue_async(apcg_cg_plan P, const CgArgs& a, const double* b, bool
   return APCG_OK;
 }
 
+// The whole solve in one cluster launch (small systems).
+apcg_status enqueue_persistent(apcg_cg_plan P, const double* b, double* x) {
+  cudaStream_t s = P->ctx->stream;
+  ClusterArgs ca{};
+  ca.rowptr = P->A.rowptr;
+  ca.col = P->A.col;
+  ca.val = static_cast<const double*>(P->A.val);
+  ca.dinv = P->dinv;
+  ca.b = b;
+  ca.x = x;
+  ca.sys = P->sys;
+  ca.order = nullptr;
+  ca.nsys = 1;
+  ca.check_every = P->k;
+  ca.next = P->next;
+  ca.res = P->sres;
+  ca.rtol = P->opts.rtol;
+  ca.atol = P->opts.atol;
+  ca.max_it = P->max_it;
+  ca.hist_len = P->hist_len;
+  ca.alpha_h = P->alpha_h;
+  ca.beta_h = P->beta_h;
+  APCG_CUDA(cudaMemsetAsync(P->next, 0, sizeof(unsigned int), s));
+  APCG_CUDA(launch_cluster_cg(ca, P->shape, 1, s));
+  count_kernels(1);
+  P->last_launches = 1;
+  APCG_CUDA(cudaMemcpyAsync(P->sres_host, P->sres, sizeof(SysResult), cudaMemcpyDeviceToHost, s));
+  counters().d2h_copies++;
+  counters().d2h_bytes += sizeof(SysResult);
+  return APCG_OK;
+}
+
 apcg_status finish_async(apcg_cg_plan P) {
   APCG_CUDA(cudaStreamSynchronize(P->ctx->stream));
   counters().host_syncs++;
@@ -563,22 +601,37 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   P->k = o.check_every;
   P->max_it = o.max_it > 0 ? o.max_it : (P->n > 0 ? 10 * P->n : 10);
   P->hist_len = o.history_len;
-  P->mode = o.mode == APCG_MODE_AUTO || o.mode == APCG_MODE_PERSISTENT ? APCG_MODE_ASYNC_GRAPH : o.mode;
+  P->mode = o.mode;
+  if (o.mode == APCG_MODE_PERSISTENT || o.mode == APCG_MODE_AUTO) {
+    P->shape = default_cluster_shape(P->n);
+    if (!P->shape.ok || P->n > kPersistentMaxRows) {
+      if (o.mode == APCG_MODE_PERSISTENT)
+        return set_error(APCG_ERR_UNSUPPORTED, "persistent mode handles at most %d rows (got %d)", kPersistentMaxRows,
+                         P->n);
+      P->mode = APCG_MODE_ASYNC_GRAPH;
+    } else {
+      P->mode = APCG_MODE_PERSISTENT;
+    }
+  }
   P->u = pick_u(A);
   const int sms = ctx_num_sms(ctx);
   const int64_t tiles = ((int64_t)P->n + 31) / 32;
   const int64_t spmv_blocks = (tiles + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t vec_blocks = (((int64_t)P->n >> 1) + kThreads - 1) / kThreads;
   void* k1 = P->u == 4 ? (void*)cg_spmv_dot_kernel<4, false> : P->u == 6 ? (void*)cg_spmv_dot_kernel<6, false> : (void*)cg_spmv_dot_kernel<8, false>;
-  P->grid_spmv = occupancy_grid(k1, sms, spmv_blocks);
-  P->grid_vec = occupancy_grid((void*)cg_update_kernel<false>, sms, vec_blocks);
+  (void)k1;
+  (void)sms;
+  auto cap = [](int64_t g) { return (int)(g < 1 ? 1 : g > dev::kMaxPartials ? dev::kMaxPartials : g); };
+  P->grid_spmv = cap(spmv_blocks);
+  P->grid_vec = cap((vec_blocks + kUpdV - 1) / kUpdV);
   // Workspace: dinv, r, p, w, z, partials, state, histories (one stream-ordered block).
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(double) * (size_t)(P->n > 0 ? P->n : 1));
   const size_t npart = up(sizeof(double) * dev::kMaxPartials * 3);
   const size_t nst = up(sizeof(CgState));
   const size_t nh = up(sizeof(double) * (size_t)(P->hist_len > 0 ? P->hist_len : 1));
-  const size_t total = 5 * nv + npart + nst + 2 * nh;
+  const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
+  const size_t total = 5 * nv + npart + nst + 2 * nh + nsysb;
   char* ws = nullptr;
   APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
   P->ws = ws;
@@ -591,7 +644,18 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   P->st = reinterpret_cast<CgState*>(ws + 5 * nv + npart);
   P->alpha_h = reinterpret_cast<double*>(ws + 5 * nv + npart + nst);
   P->beta_h = reinterpret_cast<double*>(ws + 5 * nv + npart + nst + nh);
-  APCG_CUDA(cudaMemsetAsync(ws + 5 * nv, 0, npart + nst + 2 * nh, ctx->stream));
+  char* tail = ws + 5 * nv + npart + nst + 2 * nh;
+  P->sys = reinterpret_cast<SysDesc*>(tail);
+  P->sres = reinterpret_cast<SysResult*>(tail + sizeof(SysDesc));
+  P->next = reinterpret_cast<unsigned int*>(tail + sizeof(SysDesc) + sizeof(SysResult));
+  APCG_CUDA(cudaMemsetAsync(ws + 5 * nv, 0, npart + nst + 2 * nh + nsysb, ctx->stream));
+  {
+    SysDesc d0{};
+    d0.row0 = 0;
+    d0.n = P->n;
+    APCG_CUDA(cudaMemcpyAsync(P->sys, &d0, sizeof(d0), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  APCG_CUDA(cudaMallocHost((void**)&P->sres_host, sizeof(SysResult)));
   APCG_CUDA(cudaMallocHost((void**)&P->st_host, sizeof(CgState)));
   APCG_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   {
@@ -627,10 +691,11 @@ apcg_status cg_plan_destroy(apcg_cg_plan P) {
     }
     cudaFreeAsync(P->ws, P->ctx->stream);  // stream-ordered: released once pending solves finish
   }
-  if (P->st_host) {
+  if (P->st_host || P->sres_host) {
     // Pinned memory may still be the target of an enqueued copy.
     cudaStreamSynchronize(P->ctx->stream);
-    cudaFreeHost(P->st_host);
+    if (P->st_host) cudaFreeHost(P->st_host);
+    if (P->sres_host) cudaFreeHost(P->sres_host);
   }
   delete P;
   return APCG_OK;
@@ -648,6 +713,8 @@ apcg_status cg_plan_enqueue(apcg_cg_plan P, apcg_vec b, apcg_vec x) {
   apcg_status st = APCG_OK;
   if (P->mode == APCG_MODE_HOST_SYNC)
     st = solve_host_sync(P, a, bp);
+  else if (P->mode == APCG_MODE_PERSISTENT)
+    st = enqueue_persistent(P, bp, xp);
   else
     st = enqueue_async(P, a, bp, P->mode == APCG_MODE_ASYNC_GRAPH);
   apcg_status st2 = op.finish();
@@ -660,6 +727,16 @@ apcg_status cg_plan_finish(apcg_cg_plan P, apcg_cg_result* res) {
   APCG_CHECK(P->pending, "no solve is pending on this plan");
   if (P->mode != APCG_MODE_HOST_SYNC) APCG_TRY(finish_async(P));
   P->pending = false;
+  if (P->mode == APCG_MODE_PERSISTENT) {
+    const SysResult& r = *P->sres_host;
+    CgState* h = P->st_host;
+    h->iter = r.iters;
+    h->done = r.done;
+    h->rr = r.rr;
+    h->bnorm2 = r.bnorm2;
+    if (r.done == kDoneBadDiagonal)
+      return set_error(APCG_ERR_BAD_DIAGONAL, "Jacobi: a diagonal entry is missing, zero or not finite");
+  }
   fill_result(P, res);
   return APCG_OK;
 }

@@ -6,11 +6,12 @@
 #include <cstdint>
 
 #include "apcg_internal.hpp"
+#include "cluster_cg.hpp"
 
 namespace apcg {
 
 // 'done' word of the device state block.
-enum : int32_t { kDoneRunning = 0, kDoneConverged = 1, kDoneNotConverged = 2, kDoneBreakdown = 3 };
+enum : int32_t { kDoneRunning = 0, kDoneConverged = 1, kDoneNotConverged = 2, kDoneBreakdown = 3, kDoneBadDiagonal = 4 };
 
 // Device-resident scalars of one solve (the managed scalars of Sec. 3.2).
 struct CgState {
@@ -62,4 +63,10 @@ struct apcg_cg_plan_s {
   double* graph_x = nullptr;
   bool pending = false;
   int64_t last_launches = 0;
+  // whole-solve cluster mode
+  apcg::ClusterShape shape;
+  apcg::SysDesc* sys = nullptr;          // device, one entry
+  unsigned int* next = nullptr;          // device work counter
+  apcg::SysResult* sres = nullptr;       // device
+  apcg::SysResult* sres_host = nullptr;  // pinned
 };

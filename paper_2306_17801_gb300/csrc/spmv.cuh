@@ -52,13 +52,14 @@ __device__ __forceinline__ void spmv_warp_tiles(const int32_t* __restrict__ rowp
     rs = __ldg(rowptr + rlo);
     re = __ldg(rowptr + rhi);
   };
+  const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
   int32_t rs_next = 0, re_next = 0;
   if (gwarp < ntiles) bounds(gwarp, rs_next, re_next);
   for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
     const int32_t rs = rs_next, re = re_next;
     const int32_t row = (int32_t)(tile * 32 + lane);
     T x_own = T(0);
-    if (OWN_X && row < nrows) x_own = ld_ro(x + row);
+    if (OWN_X && row < nrows) x_own = ld_ro_hint(x + row, pol_keep);
     if (tile + nwarps < ntiles) bounds(tile + nwarps, rs_next, re_next);
     const int32_t base = __shfl_sync(kFull, rs, 0);
     const int32_t end = __shfl_sync(kFull, re, 31);
@@ -70,11 +71,11 @@ __device__ __forceinline__ void spmv_warp_tiles(const int32_t* __restrict__ rowp
       for (int u = 0; u < U; ++u) {
         const int32_t e = c + u * 32 + lane;
         const bool ok = e < end;
-        j[u] = ok ? ld_stream(col + e) : -1;
-        a[u] = ok ? ld_stream(val + e) : T(0);
+        j[u] = ok ? ld_nc_hint(col + e, pol_stream) : -1;
+        a[u] = ok ? ld_nc_hint(val + e, pol_stream) : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) xv[u] = j[u] >= 0 ? ld_ro(x + j[u]) : T(0);
+      for (int u = 0; u < U; ++u) xv[u] = j[u] >= 0 ? ld_ro_hint(x + j[u], pol_keep) : T(0);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         wbuf[u * 32 + lane] = a[u];

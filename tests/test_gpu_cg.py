@@ -30,7 +30,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2306_17801_gb300 import apcg  # noqa: E402
 
-MODES = ["host_sync", "async", "async_graph"]
+MODES = ["host_sync", "async", "async_graph", "persistent"]
 
 
 @pytest.fixture(scope="module")
@@ -236,7 +236,7 @@ def test_cg_c1_parity(dev, ctx, mode):
     "name,size,k",
     [("c1", 37, 1), ("c1", 61, 7), ("c2", 23, 10), ("c3", 15, 3), ("lap27", 11, 1), ("lap9", 30, 4)],
 )
-@pytest.mark.parametrize("mode", ["async", "async_graph"])
+@pytest.mark.parametrize("mode", ["async", "async_graph", "persistent"])
 def test_cg_parity_ragged_sizes(dev, ctx, name, size, k, mode):
     p = single_problem(name, seed=3, size=size)
     ref = oracle.pcg(p.A, p.b, rtol=1e-8, check_every=k, hist_len=10)
@@ -402,4 +402,5 @@ def test_async_modes_avoid_per_iteration_syncs(dev, ctx):
     assert out["host_sync"][1]["host_syncs"] >= 2 * iters
     assert out["async"][1]["host_syncs"] <= iters // 5 + 4
     assert out["async_graph"][1]["host_syncs"] <= 3 and out["async_graph"][1]["graph_launches"] == 1
+    assert out["persistent"][1]["host_syncs"] <= 3 and out["persistent"][0]["kernel_launches"] == 1
     d.close()
