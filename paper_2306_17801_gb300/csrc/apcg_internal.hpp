@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/apcg.h"
+#include "apcg.h"
 #include "dep_tracker.hpp"
 
 namespace apcg {

@@ -73,7 +73,7 @@ namespace {
 ClusterShape shape_for_target(int n_hi, int target) {
   int C = 1;
   while (C < 16 && cluster_rows_per_cta(n_hi, C) > target) C *= 2;
-  return cluster_shape_for(n_hi, C);
+  return schedulable_shape(n_hi, C);
 }
 
 ClusterArgs class_args(apcg_batch_plan P, const BatchClass& c, const double* b, double* x) {
@@ -243,7 +243,9 @@ apcg_status apcg_batch_plan_create(apcg_ctx ctx_in, int32_t nsys, const int32_t*
                               ctx->stream));
     APCG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
     APCG_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
-    set_shape(c, shape_for_target(c.n_hi, kDefaultRowsPerCta));
+    const ClusterShape sh = shape_for_target(c.n_hi, kDefaultRowsPerCta);
+    if (!sh.ok) return set_error(APCG_ERR_UNSUPPORTED, "no schedulable cluster shape for systems of %d rows", c.n_hi);
+    set_shape(c, sh);
   }
   APCG_CUDA(cudaEventCreateWithFlags(&P->start, cudaEventDisableTiming));
   APCG_CUDA(cudaMallocHost((void**)&P->h_res, sizeof(SysResult) * nsys));

@@ -43,7 +43,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPersistentMaxRows = 65536;  // one cluster of 16 CTAs x 512 threads x 8 rows
 constexpr int kUpdV = 2;   // double2 pairs per thread in the update kernel
-constexpr int kAypxV = 2;  // double2 pairs per thread in the search-direction kernel
+constexpr int kAypxV = 4;  // double2 pairs per thread in the search-direction kernel
 
 // ------------------------------------------------------------------ kernels
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kThreads) cg_setup_kernel(CgArgs a, const doub
                                                             double atol, int32_t max_it, int32_t k,
                                                             int32_t hist_len) {
   __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
-  __shared__ double red[3 * 32];
+  __shared__ double red[3 * kThreads];
   double v[3] = {0.0, 0.0, 0.0};
   dev::spmv_warp_tiles<U, false, double>(a.rowptr, a.col, a.val, a.x, a.n, sm[threadIdx.x >> 5].buf,
                                          [&](int32_t i, double ax, double) {
@@ -108,7 +108,7 @@ template <int U, bool HOST>
 __global__ void __launch_bounds__(kThreads) cg_spmv_dot_kernel(CgArgs a) {
   if (!HOST && read_done(a.st)) return;
   __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
-  __shared__ double red[32];
+  __shared__ double red[kThreads];
   const uint64_t keep = dev::policy_evict_last();
   double v[1] = {0.0};
   dev::spmv_warp_tiles<U, true, double>(a.rowptr, a.col, a.val, a.p, a.n, sm[threadIdx.x >> 5].buf,
@@ -156,8 +156,11 @@ __global__ void __launch_bounds__(kThreads, 4) cg_update_kernel(CgArgs a, double
     const int32_t it = a.st->iter + 1;
     check = (it % a.st->check_every == 0) || it >= a.st->max_it;
   }
-  __shared__ double red[2 * 32];
+  __shared__ double red[2 * kThreads];
   double v[2] = {0.0, 0.0};
+  double acc_rz[kUpdV], acc_rr[kUpdV];  // independent chains, combined in a fixed order below
+#pragma unroll
+  for (int u = 0; u < kUpdV; ++u) acc_rz[u] = acc_rr[u] = 0.0;
   const int64_t n = a.n, np = n >> 1, stride = (int64_t)gridDim.x * blockDim.x;
   double2* x2 = reinterpret_cast<double2*>(a.x);
   double2* r2 = reinterpret_cast<double2*>(a.r);
@@ -193,11 +196,11 @@ __global__ void __launch_bounds__(kThreads, 4) cg_update_kernel(CgArgs a, double
           dev::st2_hint(x2 + i, xx[u], keep);
           dev::st2_hint(r2 + i, rr[u], keep);
           dev::st2_hint(z2 + i, zz, keep);
-          v[0] = fma(rr[u].x, zz.x, v[0]);
-          v[0] = fma(rr[u].y, zz.y, v[0]);
+          acc_rz[u] = fma(rr[u].x, zz.x, acc_rz[u]);
+          acc_rz[u] = fma(rr[u].y, zz.y, acc_rz[u]);
           if (decltype(with_rr)::value) {
-            v[1] = fma(rr[u].x, rr[u].x, v[1]);
-            v[1] = fma(rr[u].y, rr[u].y, v[1]);
+            acc_rr[u] = fma(rr[u].x, rr[u].x, acc_rr[u]);
+            acc_rr[u] = fma(rr[u].y, rr[u].y, acc_rr[u]);
           }
         }
       }
@@ -207,6 +210,11 @@ __global__ void __launch_bounds__(kThreads, 4) cg_update_kernel(CgArgs a, double
     sweep(std::true_type{});
   else
     sweep(std::false_type{});
+#pragma unroll
+  for (int u = 0; u < kUpdV; ++u) {
+    v[0] += acc_rz[u];
+    v[1] += acc_rr[u];
+  }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t i = n - 1;
     a.x[i] = fma(alpha, a.p[i], a.x[i]);
@@ -619,11 +627,8 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   const int64_t spmv_blocks = (tiles + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t vec_blocks = (((int64_t)P->n >> 1) + kThreads - 1) / kThreads;
   void* k1 = P->u == 4 ? (void*)cg_spmv_dot_kernel<4, false> : P->u == 6 ? (void*)cg_spmv_dot_kernel<6, false> : (void*)cg_spmv_dot_kernel<8, false>;
-  (void)k1;
-  (void)sms;
-  auto cap = [](int64_t g) { return (int)(g < 1 ? 1 : g > dev::kMaxPartials ? dev::kMaxPartials : g); };
-  P->grid_spmv = cap(spmv_blocks);
-  P->grid_vec = cap((vec_blocks + kUpdV - 1) / kUpdV);
+  P->grid_spmv = occupancy_grid(k1, sms, spmv_blocks);
+  P->grid_vec = occupancy_grid((void*)cg_update_kernel<false>, sms, (vec_blocks + kUpdV - 1) / kUpdV);
   // Workspace: dinv, r, p, w, z, partials, state, histories (one stream-ordered block).
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(double) * (size_t)(P->n > 0 ? P->n : 1));

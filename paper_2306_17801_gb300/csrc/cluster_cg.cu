@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(ClusterArgs
   const int tpb = blockDim.x;
   extern __shared__ double s_p[];  // this CTA's slice of p
   __shared__ double s_slot[2][4];
-  __shared__ double s_red[4 * 32];
+  __shared__ double s_red[4 * kClusterThreads];
   __shared__ double s_tot[4];
   __shared__ double* s_peer[kMaxCluster];
   __shared__ double* s_peer_slot[kMaxCluster];
@@ -272,11 +272,11 @@ int max_clusters_r(const ClusterShape& sh) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
-    n = 1;
+    n = 0;
   }
-  return n;
+  return n;  // 0: this shape cannot be scheduled on this device
 }
 
 }  // namespace
@@ -299,12 +299,20 @@ ClusterShape cluster_shape_for(int n_max, int C) {
   return sh;
 }
 
+ClusterShape schedulable_shape(int n_max, int C) {
+  // Halve the cluster until the device can hold one; larger slices per CTA follow.
+  ClusterShape sh = cluster_shape_for(n_max, C);
+  while (sh.ok && sh.C > 1 && max_active_clusters(sh) < 1) sh = cluster_shape_for(n_max, sh.C / 2);
+  if (sh.ok && max_active_clusters(sh) < 1) sh.ok = false;
+  return sh;
+}
+
 ClusterShape default_cluster_shape(int n) {
   // Spread small systems over as many SMs as a cluster has (the float64 pipe
   // of one SM retires two lanes per cycle), keeping at least 256 rows per CTA.
   int C = 1;
   while (C < kMaxCluster && cluster_rows_per_cta(n, C) > 256) C *= 2;
-  return cluster_shape_for(n, C);
+  return schedulable_shape(n, C);
 }
 
 cudaError_t launch_cluster_cg(const ClusterArgs& args, const ClusterShape& sh, int nclusters, cudaStream_t s) {

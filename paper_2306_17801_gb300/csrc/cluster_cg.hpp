@@ -54,7 +54,10 @@ struct ClusterShape {
 int cluster_rows_per_cta(int n, int C);
 ClusterShape cluster_shape_for(int n_max, int C);
 ClusterShape default_cluster_shape(int n);
+// The shape for C CTAs per cluster, halving C until the device can schedule it (ok = false if none).
+ClusterShape schedulable_shape(int n_max, int C);
 cudaError_t launch_cluster_cg(const ClusterArgs& args, const ClusterShape& sh, int nclusters, cudaStream_t s);
+// Clusters of this shape that fit on the device at once (0: not schedulable).
 int max_active_clusters(const ClusterShape& sh);
 
 }  // namespace apcg

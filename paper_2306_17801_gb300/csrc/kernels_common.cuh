@@ -92,23 +92,24 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;  // valid in lane 0
 }
 
-// Sum NV values over the block in a fixed order (lanes, then warps).  smem
-// must hold NV*32 values.  Thread 0 receives the totals in v[].
+// Sum NV values over the block in a fixed order.  On GB300 every float64
+// add is scarce (the float64 pipe retires two lanes per SM per cycle), so the
+// tree is not built from shuffles in every warp: each thread parks its values
+// in shared memory, lane l of warp 0 adds the values of threads l, l+32, ...
+// in order, and one shuffle tree in warp 0 finishes.  smem must hold
+// NV * blockDim.x values.  Thread 0 receives the totals in v[].
 template <int NV, class T>
 __device__ __forceinline__ void block_sum(T (&v)[NV], T* smem) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  const int nt = blockDim.x;
   __syncthreads();  // smem may still be read by a previous call
-  if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) smem[k * 32 + warp] = v[k];
-  }
+  for (int k = 0; k < NV; ++k) smem[k * nt + threadIdx.x] = v[k];
   __syncthreads();
-  if (warp == 0) {
+  if (threadIdx.x < 32) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      T t = lane < nw ? smem[k * 32 + lane] : T(0);
+      T t = T(0);
+      for (int i = threadIdx.x; i < nt; i += 32) t += smem[k * nt + i];
       v[k] = warp_sum(t);
     }
   }
@@ -118,7 +119,8 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* smem) {
 // NV block sums to partials[k * gridDim.x + blockIdx.x]; the block that
 // arrives last (atomic ticket) sums the partials in block order and returns
 // true; only its thread 0 holds valid totals in tot[].  The ticket is reset
-// to zero for the next kernel.  partials must hold NV * gridDim.x values.
+// to zero for the next kernel.  partials must hold NV * gridDim.x values and
+// smem NV * blockDim.x values.
 template <int NV, class T>
 __device__ __forceinline__ bool grid_sum_last(T (&v)[NV], T* partials, unsigned int* ticket, T* smem, T (&tot)[NV]) {
   __shared__ bool s_last;

@@ -33,7 +33,7 @@ int vec_grid(apcg_ctx ctx, int64_t n_pairs, int cap) {
 __global__ void __launch_bounds__(kVecThreads) dot_kernel(int64_t n, const double* __restrict__ x,
                                                           const double* __restrict__ y, double* out, int take_sqrt,
                                                           double* partials, unsigned int* ticket) {
-  __shared__ double smem[32];
+  __shared__ double smem[kVecThreads];
   double v[1] = {0.0};
   const int64_t np = n >> 1, stride = (int64_t)gridDim.x * blockDim.x;
   const double2* x2 = reinterpret_cast<const double2*>(x);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_kernel(const int32_t* __res
                                                             const double* __restrict__ x, double* __restrict__ y,
                                                             double* out, double* partials, unsigned int* ticket) {
   __shared__ dev::SpmvSmem<U, double> sm[kSpmvThreads / 32];
-  __shared__ double red[32];
+  __shared__ double red[kSpmvThreads];
   double v[1] = {0.0};
   dev::spmv_warp_tiles<U, DOT, double>(rowptr, col, val, x, nrows, sm[threadIdx.x >> 5].buf,
                                        [&](int32_t row, double s, double x_row) {
