@@ -396,6 +396,38 @@ APCG_API apcg_status apcg_cg_plan_profile(apcg_cg_plan plan, apcg_vec b, apcg_ve
 APCG_API apcg_status apcg_cg_solve_host(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const double* val,
                                const double* b, double* x, const apcg_cg_opts* opts, apcg_cg_result* res);
 
+/*
+ * Jacobi-PCG without any device allocation (the paper has no counterpart;
+ * this entry point exists for callers that cannot allocate).  Some callers
+ * cannot call cudaMalloc when they solve: a framework that reserved nearly
+ * all device memory for its own pool leaves none for a library allocation,
+ * and a real-time loop must not allocate after start-up because a device
+ * allocation may synchronise the device and takes unbounded time.  This call
+ * solves one system with the whole-solve cluster kernel (the PERSISTENT mode
+ * of apcg_cg_solve) and keeps its scratch -- the Jacobi diagonal and the
+ * solve's bookkeeping -- in a fixed array inside the library, which every GPU
+ * that loads the library holds until the process exits.  It allocates no
+ * device memory, creates no stream or context, and does no intent marking.
+ *
+ * cuda_stream: the caller's cudaStream_t (NULL selects the legacy default
+ * stream); the work is ordered on it and the call blocks until it finishes.
+ * rowptr/col/val, b, x: device CSR matrix and vectors as for apcg_cg_solve
+ * (x holds x0 on entry).  opts: rtol, atol, max_it, check_every (mode and
+ * history are ignored); NULL selects the defaults.  res: host, filled at exit.
+ *
+ * Limit: n <= 65536 rows (the size of the fixed array); larger n returns
+ * APCG_ERR_INVALID_ARG before anything is enqueued.  Every call shares the
+ * one array, which keeps the last call's contents (each call rewrites what it
+ * reads): calls that overlap on the GPU -- on different streams or from
+ * different host threads -- race and must not be issued.  The first call on
+ * each device looks up the array's device address; make that first call
+ * before any stream capture.  Returns APCG_ERR_BAD_DIAGONAL for a zero,
+ * missing or non-finite diagonal entry.
+ */
+APCG_API apcg_status apcg_cg_solve_noalloc(void* cuda_stream, int32_t n, int64_t nnz, const int32_t* rowptr,
+                                           const int32_t* col, const double* val, const double* b, double* x,
+                                           const apcg_cg_opts* opts, apcg_cg_result* res);
+
 /* ------------------------------------------------------------------ batched solves (many independent systems) */
 
 /*

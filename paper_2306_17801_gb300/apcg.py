@@ -172,6 +172,7 @@ PROTOS = {
     "apcg_cg_plan_destroy": [P],
     "apcg_cg_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
     "apcg_cg_solve_host": [i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
+    "apcg_cg_solve_noalloc": [P, i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
     "apcg_batch_plan_create": [P, i32, P, P, P, P, C.POINTER(CgOpts), PP],
     "apcg_batch_plan_solve": [P, P, P, P],
     "apcg_batch_plan_tune": [P, P, C.c_char_p, C.c_size_t],
@@ -439,6 +440,17 @@ def batch_plan_tune(plan, b) -> list[tuple]:
         f = line.split()
         rows.append({"n_lo": int(f[0]), "n_hi": int(f[1]), "cluster": int(f[2]), "threads": int(f[3]), "rows_per_thread": int(f[4]), "ms": float(f[5])})
     return rows
+
+
+def cg_solve_noalloc(stream, rowptr, col, val, b, x, opts: CgOpts) -> dict:
+    """Solve through the entry point that allocates no device memory (CUDA tensors; x updated in place)."""
+    s = 0 if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    res = CgResult()
+    call(
+        "apcg_cg_solve_noalloc", C.c_void_p(s), rowptr.numel() - 1, col.numel(), C.c_void_p(_ptr(rowptr)),
+        C.c_void_p(_ptr(col)), C.c_void_p(_ptr(val)), C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x)), C.byref(opts), C.byref(res),
+    )
+    return res.as_dict()
 
 
 def get_counters() -> dict:
