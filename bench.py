@@ -434,6 +434,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="only the set-up and 3 iterations, kernels launched one by one (for profilers)")
+    ap.add_argument("--config", choices=["c2", "c3", "c4"], default="c2",
+                    help="c2: the headline 128^3 workload (default); c3/c4: extra measurement lines")
+    ap.add_argument("--no-tune", action="store_true", help="c4: skip the batched autotuner")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
@@ -453,7 +456,149 @@ def main():
     if args.ncu_case:
         ncu_case()
         return
+    if args.config != "c2":
+        {"c3": bench_c3, "c4": bench_c4}[args.config](args)
+        return
     run_apcg(args, rank, world, local)
+
+
+def _gpu_problem(p, dev):
+    import numpy as np
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d = {"rowptr": t(p.A.rowptr), "col": t(p.A.col), "val": t(p.A.val), "b": t(p.b)}
+    d["x"] = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    d["A"] = apcg.mat_wrap(d["rowptr"], d["col"], d["val"])
+    d["vb"], d["vx"] = apcg.vec_wrap(d["b"]), apcg.vec_wrap(d["x"])
+    return d
+
+
+def bench_c3(args):
+    """160^3 variable-coefficient 27-point: float64 PCG vs float32-inner refinement, both to rtol 1e-10."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+    from synthetic import single_problem
+
+    V = C.c_void_p
+    dev = torch.device("cuda", 0)
+    apcg.load()
+    p = single_problem("c3", seed=0)
+    n, nnz = p.n, p.nnz
+    g = _gpu_problem(p, dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = apcg.ctx_create(stream)
+    out = {"config": {"workload": "3D 27-point variable-kappa diffusion 160^3 (n=4,096,000, nnz=109,215,352), rtol 1e-10"}}
+
+    def timed(fn, reps):
+        best, r = None, None
+        for i in range(reps + 1):
+            apcg.call("apcg_vec_set_async", V(ctx), V(g["vx"]), C.c_double(0.0))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if i > 0:
+                best = ms if best is None else min(best, ms)
+        return best, r
+
+    plan = apcg.cg_plan_create(ctx, g["A"], apcg.cg_opts(rtol=1e-10, check_every=10, mode="async_graph", max_it=50000))
+    ms64, r64 = timed(lambda: apcg.cg_plan_solve(plan, g["vb"], g["vx"]), max(1, args.steps // 3))
+    apcg.call("apcg_cg_plan_destroy", V(plan))
+    b_it64 = 12 * nnz + 4 * (n + 1) + 104 * n
+    out["fp64_pcg"] = {
+        "ms_per_solve": ms64, "iters": r64["iters"], "us_per_iteration": 1e3 * ms64 / r64["iters"],
+        "GBps_per_iteration": b_it64 / (1e-3 * ms64 / r64["iters"]) / 1e9, "rel_res": r64["rel_res"],
+    }
+    irp = apcg.ir_plan_create(ctx, g["A"], None, apcg.ir_opts(rtol=1e-10, rtol_inner=1e-4, inner_check_every=10))
+    msir, rir = timed(lambda: apcg.ir_plan_solve(irp, g["vb"], g["vx"]), max(1, args.steps // 3))
+    apcg.call("apcg_ir_plan_destroy", V(irp))
+    b_it32 = 8 * nnz + 4 * (n + 1) + 52 * n
+    out["mixed_ir"] = {
+        "ms_per_solve": msir, "outer": rir["outer"], "inner_total": rir["inner_total"],
+        "us_per_inner_iteration": 1e3 * msir / max(1, rir["inner_total"]),
+        "GBps_per_inner_iteration": b_it32 / (1e-3 * msir / max(1, rir["inner_total"])) / 1e9, "rel_res": rir["rel_res"],
+    }
+    out["speedup_ir_vs_fp64"] = ms64 / msir
+    line = {"metric": "time to solution at rtol 1e-10 (float64 PCG vs float32-inner refinement)", "value": 1e3 / msir,
+            "unit": "solves/s", "dtype": "f32+f64", "data": "synthetic", **out}
+    print(json.dumps(line), flush=True)
+
+
+def bench_c4(args):
+    """1024 shifted 5-point systems (sides 16..128): one batched graph launch vs one solve at a time (float64)."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+    from synthetic import batch_shifted_5pt
+
+    V = C.c_void_p
+    dev = torch.device("cuda", 0)
+    apcg.load()
+    B = batch_shifted_5pt(1024, seed=0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rowptr, col, val, b = t(B.rowptr), t(B.col), t(B.val), t(B.b)
+    x = torch.zeros(B.n_total, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = apcg.ctx_create(stream)
+    out = {"config": {"workload": "1024 x (2D 5-point + sigma I), sides 16..128 (6.40 M rows), rtol 1e-8, k=1"}}
+    opts = apcg.cg_opts(rtol=1e-8, check_every=1)
+    plan = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, val, opts)
+    table = apcg.batch_plan_tune(plan, b) if not args.no_tune else None
+
+    def batched():
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = apcg.batch_plan_solve(plan, b, x, B.nsys)
+        return time.perf_counter() - t0, res
+
+    batched()
+    dts = [batched() for _ in range(max(2, args.steps // 3))]
+    dt, res = min(dts, key=lambda z: z[0])
+    iters = np.array([r["iters"] for r in res])
+    assert all(r["reason"] == "converged" for r in res)
+    out["batched"] = {"ms_per_batch": 1e3 * dt, "solves_per_s": B.nsys / dt, "iters_total": int(iters.sum()),
+                      "iters_max": int(iters.max()), "tuning_table": table}
+    apcg.call("apcg_batch_plan_destroy", V(plan))
+    # one system at a time through the single-system solver (its best mode: the persistent
+    # cluster kernel); every system's arrays and plan are prepared before the clock starts
+    sizes = np.diff(B.sys_row_off)
+    systems = []
+    for s in range(B.nsys):
+        A_s, b_s, _ = B.system(s)
+        d = {"rowptr": t(A_s.rowptr), "col": t(A_s.col), "val": t(A_s.val), "b": t(b_s)}
+        d["x"] = torch.zeros(A_s.n, dtype=torch.float64, device=dev)
+        d["A"] = apcg.mat_wrap(d["rowptr"], d["col"], d["val"])
+        d["vb"], d["vx"] = apcg.vec_wrap(d["b"]), apcg.vec_wrap(d["x"])
+        d["plan"] = apcg.cg_plan_create(ctx, d["A"], apcg.cg_opts(rtol=1e-8, check_every=1, mode="auto"))
+        systems.append(d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d in systems:
+        r = apcg.cg_plan_solve(d["plan"], d["vb"], d["vx"])
+        assert r["reason"] == "converged"
+    dt_seq = time.perf_counter() - t0
+    for d in systems:
+        apcg.call("apcg_cg_plan_destroy", V(d["plan"]))
+        for h, fn in ((d["vb"], "apcg_vec_destroy"), (d["vx"], "apcg_vec_destroy"), (d["A"], "apcg_mat_destroy")):
+            apcg.call(fn, V(h))
+    out["one_at_a_time"] = {"ms_per_batch": 1e3 * dt_seq, "solves_per_s": B.nsys / dt_seq, "max_rows": int(sizes.max())}
+    out["speedup_batched_vs_one_at_a_time"] = dt_seq / dt
+    line = {"metric": "batched PCG solves/s at rtol 1e-8 (FP64)", "value": B.nsys / dt, "unit": "solves/s",
+            "dtype": "f64", "data": "synthetic", **out}
+    print(json.dumps(line), flush=True)
 
 
 def ncu_case():

@@ -428,6 +428,51 @@ APCG_API apcg_status apcg_cg_solve_noalloc(void* cuda_stream, int32_t n, int64_t
                                            const int32_t* col, const double* val, const double* b, double* x,
                                            const apcg_cg_opts* opts, apcg_cg_result* res);
 
+/* ------------------------------------------------------------------ mixed-precision iterative refinement */
+
+/*
+ * float64 iterative refinement around a float32 Jacobi-PCG (an extension of
+ * the paper's float64 CG, Sec. 4.2; not in the paper).  float64 is kept only
+ * for the outer residual r = b - A x, the update x += d and the convergence
+ * norm; the inner PCG on A d = r runs in float32 (values, vectors, FMAs and
+ * accumulation) from d = 0 until ||r_in|| <= rtol_inner ||(float) r||, or
+ * max_inner iterations.  Outer stop: ||b - A x||_2 <= max(rtol ||b||_2, atol)
+ * with the true residual in float64.
+ *
+ * A64: float64 CSR (device) used for the outer residual; may be NULL when the
+ * float32 values are exact copies (the outer residual then widens them).
+ * A32: float32 CSR with the same rowptr/col arrays; may be NULL, in which case
+ * the plan keeps a round-to-nearest float32 copy of A64's values.
+ */
+typedef struct apcg_ir_plan_s* apcg_ir_plan;
+
+typedef struct {
+  double rtol;               /* outer relative tolerance (default 1e-10) */
+  double atol;               /* outer absolute tolerance (default 0) */
+  int32_t max_outer;         /* corrections (default 50) */
+  int32_t max_inner;         /* inner iterations per correction (default 1000) */
+  float rtol_inner;          /* inner relative tolerance (default 1e-4) */
+  int32_t inner_check_every; /* inner convergence test every k iterations (default 1) */
+} apcg_ir_opts;
+
+typedef struct {
+  int32_t outer;            /* corrections applied */
+  int32_t inner_total;      /* inner iterations summed over corrections */
+  int32_t reason;           /* apcg_reason */
+  int32_t pad;
+  double rel_res;           /* ||b - A x|| / ||b|| at exit (float64 true residual) */
+  int64_t kernel_launches;  /* kernels executed */
+} apcg_ir_result;
+
+APCG_API apcg_status apcg_ir_opts_default(apcg_ir_opts* opts);
+APCG_API apcg_status apcg_ir_plan_create(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, const apcg_ir_opts* opts,
+                                         apcg_ir_plan* out);
+/* Solve A x = b (x holds x0 on entry).  Blocks once per correction to read two norms. */
+APCG_API apcg_status apcg_ir_plan_solve(apcg_ir_plan plan, apcg_vec b, apcg_vec x, apcg_ir_result* res);
+APCG_API apcg_status apcg_ir_plan_destroy(apcg_ir_plan plan);
+APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
+                                   const apcg_ir_opts* opts, apcg_ir_result* res);
+
 /* ------------------------------------------------------------------ batched solves (many independent systems) */
 
 /*

@@ -98,6 +98,37 @@ class CgResult(C.Structure):
         }
 
 
+class IrOpts(C.Structure):
+    _fields_ = [
+        ("rtol", C.c_double),
+        ("atol", C.c_double),
+        ("max_outer", C.c_int32),
+        ("max_inner", C.c_int32),
+        ("rtol_inner", C.c_float),
+        ("inner_check_every", C.c_int32),
+    ]
+
+
+class IrResult(C.Structure):
+    _fields_ = [
+        ("outer", C.c_int32),
+        ("inner_total", C.c_int32),
+        ("reason", C.c_int32),
+        ("pad", C.c_int32),
+        ("rel_res", C.c_double),
+        ("kernel_launches", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {
+            "outer": int(self.outer),
+            "inner_total": int(self.inner_total),
+            "reason": REASONS.get(int(self.reason), int(self.reason)),
+            "rel_res": float(self.rel_res),
+            "kernel_launches": int(self.kernel_launches),
+        }
+
+
 class BatchResult(C.Structure):
     _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rel_res", C.c_double)]
 
@@ -173,6 +204,11 @@ PROTOS = {
     "apcg_cg_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
     "apcg_cg_solve_host": [i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
     "apcg_cg_solve_noalloc": [P, i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
+    "apcg_ir_opts_default": [C.POINTER(IrOpts)],
+    "apcg_ir_plan_create": [P, P, P, C.POINTER(IrOpts), PP],
+    "apcg_ir_plan_solve": [P, P, P, C.POINTER(IrResult)],
+    "apcg_ir_plan_destroy": [P],
+    "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
     "apcg_batch_plan_create": [P, i32, P, P, P, P, C.POINTER(CgOpts), PP],
     "apcg_batch_plan_solve": [P, P, P, P],
     "apcg_batch_plan_tune": [P, P, C.c_char_p, C.c_size_t],
@@ -450,6 +486,26 @@ def cg_solve_noalloc(stream, rowptr, col, val, b, x, opts: CgOpts) -> dict:
         "apcg_cg_solve_noalloc", C.c_void_p(s), rowptr.numel() - 1, col.numel(), C.c_void_p(_ptr(rowptr)),
         C.c_void_p(_ptr(col)), C.c_void_p(_ptr(val)), C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x)), C.byref(opts), C.byref(res),
     )
+    return res.as_dict()
+
+
+def ir_opts(rtol=1e-10, atol=0.0, max_outer=50, max_inner=1000, rtol_inner=1e-4, inner_check_every=1):
+    o = IrOpts()
+    call("apcg_ir_opts_default", C.byref(o))
+    o.rtol, o.atol, o.max_outer, o.max_inner = rtol, atol, max_outer, max_inner
+    o.rtol_inner, o.inner_check_every = rtol_inner, inner_check_every
+    return o
+
+
+def ir_plan_create(ctx, A64, A32, opts: IrOpts):
+    h = _out()
+    call("apcg_ir_plan_create", C.c_void_p(ctx), C.c_void_p(A64), C.c_void_p(A32), C.byref(opts), C.byref(h))
+    return h.value
+
+
+def ir_plan_solve(plan, b, x) -> dict:
+    res = IrResult()
+    call("apcg_ir_plan_solve", C.c_void_p(plan), C.c_void_p(b), C.c_void_p(x), C.byref(res))
     return res.as_dict()
 
 

@@ -1,0 +1,464 @@
+// The three iteration kernels of Jacobi-PCG, for float64 and float32.
+//
+// The method is textbook Hestenes-Stiefel PCG with diagonal scaling (Sec. 4.1,
+// 4.2), its loop body in the order of the mixed-API CG example of Sec. 3.3:
+//   w = A p;  gamma = (p,w);  alpha = rho / gamma
+//   x += alpha p;  r -= alpha w;  z = D^-1 r;  rho' = (r,z);  rr = (r,r)
+//   convergence test every k-th iteration:  sqrt(rr) <= tol
+//   beta = rho' / rho;  p = z + beta p;  rho = rho'
+// One iteration is three kernels, each fusing the work between two global
+// reductions:
+//   K1  w = A p and the partial sums of (p,w); the last block forms gamma and
+//       alpha = rho / gamma (or flags a breakdown);
+//   K2  x += alpha p, r -= alpha w, z = D^-1 r (stored for K3), the partial
+//       sums of (r,z) and, on test iterations, (r,r); the last block counts
+//       the iteration, runs the test and forms beta;
+//   K3  p = z + beta p.
+// alpha, beta, rho and the residual norm live in the device state block;
+// every kernel starts by reading the 'done' word and returns at once when the
+// solve has finished (the semaphore idea of Sec. 5).  Arithmetic and
+// accumulation are in T: float64 for the CG solver, float32 for the inner
+// solver of mixed-precision refinement; scalars are stored in the state block
+// as double (exact for float).  On GB300 the float64 pipe (two lanes per SM
+// per cycle) is as scarce as HBM bandwidth, so the float64 kernels spend
+// one FMA per nonzero in K1, four float64 operations per row in K2 (five on
+// test iterations) and one in K3.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "cg_core.hpp"
+#include "kernels_common.cuh"
+#include "spmv.cuh"
+
+namespace apcg {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUpdV = 2;   // 16-byte vectors per thread and array in K2
+constexpr int kAypxV = 4;  // 16-byte vectors per thread and array in K3
+
+// 16-byte vector of T: double2 or float4.
+template <class T>
+struct V16;
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int E = 2;
+};
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int E = 4;
+};
+
+template <class T>
+struct Args {
+  const int32_t* __restrict__ rowptr;
+  const int32_t* __restrict__ col;
+  const T* __restrict__ val;
+  int32_t n;
+  const T* __restrict__ dinv;
+  T* x;
+  T* r;
+  T* p;
+  T* w;
+  T* z;
+  CgState* st;
+  T* partials;
+  double* alpha_h;
+  double* beta_h;
+};
+
+template <class T>
+Args<T> make_args(const CgCore<T>& c, T* x) {
+  Args<T> a;
+  a.rowptr = c.rowptr;
+  a.col = c.col;
+  a.val = c.val;
+  a.n = c.n;
+  a.dinv = c.dinv;
+  a.x = x;
+  a.r = c.r;
+  a.p = c.p;
+  a.w = c.w;
+  a.z = c.z;
+  a.st = c.st;
+  a.partials = c.partials;
+  a.alpha_h = c.alpha_h;
+  a.beta_h = c.beta_h;
+  return a;
+}
+
+__device__ __forceinline__ int32_t read_done(const CgState* st) { return *(volatile const int32_t*)&st->done; }
+
+// r = b - A x0, z = D^-1 r, p = z; rho = (r,z), rr = (r,r), bb = (b,b) (float64 solve).
+template <int U>
+__global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const double* __restrict__ b, double rtol,
+                                                         double atol, int32_t max_it, int32_t k, int32_t hist_len) {
+  __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
+  __shared__ double red[3 * kThreads];
+  double v[3] = {0.0, 0.0, 0.0};
+  dev::spmv_warp_tiles<U, false, double>(a.rowptr, a.col, a.val, a.x, a.n, sm[threadIdx.x >> 5].buf,
+                                         [&](int32_t i, double ax, double) {
+                                           const double bi = __ldg(b + i);
+                                           const double ri = bi - ax;
+                                           const double zi = __ldg(a.dinv + i) * ri;
+                                           a.r[i] = ri;
+                                           a.p[i] = zi;
+                                           v[0] = fma(ri, zi, v[0]);
+                                           v[1] = fma(ri, ri, v[1]);
+                                           v[2] = fma(bi, bi, v[2]);
+                                         });
+  double tot[3];
+  if (dev::grid_sum_last<3>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    CgState* st = a.st;
+    st->rho = tot[0];
+    st->rr = tot[1];
+    st->bnorm2 = tot[2];
+    const double tol = fmax(rtol * sqrt(tot[2]), atol);
+    st->tol = tol;
+    st->iter = 0;
+    st->max_it = max_it;
+    st->check_every = k;
+    st->hist_len = hist_len;
+    st->body_runs = 0;
+    st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
+    st->done = (sqrt(tot[1]) <= tol) ? kDoneConverged : 0;
+  }
+}
+
+// K1
+template <int U, bool HOST, class T>
+__global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
+  if (!HOST && read_done(a.st)) return;
+  __shared__ dev::SpmvSmem<U, T> sm[kThreads / 32];
+  __shared__ T red[kThreads];
+  T v[1] = {T(0)};
+  dev::spmv_warp_tiles<U, true, T>(a.rowptr, a.col, a.val, a.p, a.n, sm[threadIdx.x >> 5].buf,
+                                   [&](int32_t i, T s, T p_i) {
+                                     a.w[i] = s;
+                                     v[0] = fma(p_i, s, v[0]);
+                                   });
+  T tot[1];
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    CgState* st = a.st;
+    const T gamma = tot[0];
+    st->gamma = gamma;
+    if (!HOST) {
+      if (!(gamma > T(0)) || !isfinite(gamma)) {
+        st->done = kDoneBreakdown;
+      } else {
+        const T alpha = (T)st->rho / gamma;
+        st->alpha = alpha;
+        if (st->iter < st->hist_len) a.alpha_h[st->iter] = alpha;
+      }
+    }
+  }
+}
+
+// K2.  The test runs when the iteration count is a multiple of k or reaches
+// max_it, decided from the state block at kernel entry, so one kernel serves
+// every position of a captured block.
+template <bool HOST, class T>
+__global__ void __launch_bounds__(kThreads, 4) k2_kernel(Args<T> a, double alpha_host, cudaGraphConditionalHandle cond,
+                                                         int32_t use_cond) {
+  using VT = typename V16<T>::type;
+  constexpr int E = V16<T>::E;
+  if (!HOST && read_done(a.st)) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+      a.st->body_runs += 1;
+      cudaGraphSetConditional(cond, 0u);
+    }
+    return;
+  }
+  const T alpha = HOST ? (T)alpha_host : (T)a.st->alpha;
+  bool check = true;
+  if (!HOST) {
+    const int32_t it = a.st->iter + 1;
+    check = (it % a.st->check_every == 0) || it >= a.st->max_it;
+  }
+  __shared__ T red[2 * kThreads];
+  T v[2] = {T(0), T(0)};
+  T acc_rz[kUpdV], acc_rr[kUpdV];  // independent chains, combined in a fixed order below
+#pragma unroll
+  for (int u = 0; u < kUpdV; ++u) acc_rz[u] = acc_rr[u] = T(0);
+  const int64_t n = a.n, nv = n / E, stride = (int64_t)gridDim.x * blockDim.x;
+  VT* xv = reinterpret_cast<VT*>(a.x);
+  VT* rv = reinterpret_cast<VT*>(a.r);
+  VT* zv = reinterpret_cast<VT*>(a.z);
+  const VT* pv = reinterpret_cast<const VT*>(a.p);
+  const VT* wv = reinterpret_cast<const VT*>(a.w);
+  const VT* dv = reinterpret_cast<const VT*>(a.dinv);
+  auto sweep = [&](auto with_rr) {
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nv; i0 += kUpdV * stride) {
+      VT xx[kUpdV], rr[kUpdV], pp[kUpdV], ww[kUpdV], dd[kUpdV];
+#pragma unroll
+      for (int u = 0; u < kUpdV; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < nv) {
+          xx[u] = xv[i];
+          rr[u] = rv[i];
+          pp[u] = __ldg(pv + i);
+          ww[u] = dev::ld_stream2(wv + i);
+          dd[u] = __ldg(dv + i);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUpdV; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < nv) {
+          T* xe = reinterpret_cast<T*>(&xx[u]);
+          T* re = reinterpret_cast<T*>(&rr[u]);
+          const T* pe = reinterpret_cast<const T*>(&pp[u]);
+          const T* we = reinterpret_cast<const T*>(&ww[u]);
+          const T* de = reinterpret_cast<const T*>(&dd[u]);
+          VT zz;
+          T* ze = reinterpret_cast<T*>(&zz);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            xe[e] = fma(alpha, pe[e], xe[e]);
+            re[e] = fma(-alpha, we[e], re[e]);
+            ze[e] = de[e] * re[e];
+            acc_rz[u] = fma(re[e], ze[e], acc_rz[u]);
+            if (decltype(with_rr)::value) acc_rr[u] = fma(re[e], re[e], acc_rr[u]);
+          }
+          xv[i] = xx[u];
+          rv[i] = rr[u];
+          zv[i] = zz;
+        }
+      }
+    }
+  };
+  if (check)
+    sweep(std::true_type{});
+  else
+    sweep(std::false_type{});
+#pragma unroll
+  for (int u = 0; u < kUpdV; ++u) {
+    v[0] += acc_rz[u];
+    v[1] += acc_rr[u];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int64_t i = nv * E; i < n; ++i) {
+      a.x[i] = fma(alpha, a.p[i], a.x[i]);
+      const T ri = fma(-alpha, a.w[i], a.r[i]);
+      const T zi = a.dinv[i] * ri;
+      a.r[i] = ri;
+      a.z[i] = zi;
+      v[0] = fma(ri, zi, v[0]);
+      if (check) v[1] = fma(ri, ri, v[1]);
+    }
+  }
+  T tot[2];
+  if (dev::grid_sum_last<2>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    CgState* st = a.st;
+    const T rz = tot[0], rr = tot[1];
+    st->rho_new = rz;
+    if (check) st->rr = rr;
+    if (!HOST) {
+      const int32_t it = st->iter + 1;
+      st->iter = it;
+      int32_t done = 0;
+      // An exactly zero residual ends the solve at any iteration; between
+      // tests (r, D^-1 r) = 0 stands for r = 0 (D^-1 is positive).
+      if ((check && rr == T(0)) || rz == T(0))
+        done = kDoneConverged;
+      else if (check && sqrt(rr) <= (T)st->tol)
+        done = kDoneConverged;
+      else if (it >= st->max_it)
+        done = kDoneNotConverged;
+      else if (!isfinite(rz) || (check && !isfinite(rr)))
+        done = kDoneBreakdown;
+      if (!done) {
+        const T beta = rz / (T)st->rho;
+        st->beta = beta;
+        st->rho = rz;
+        if (it - 1 < st->hist_len) a.beta_h[it - 1] = beta;
+      }
+      st->done = done;
+      if (use_cond) {
+        st->body_runs += 1;
+        cudaGraphSetConditional(cond, done ? 0u : 1u);
+      }
+    }
+  }
+}
+
+// K3: p = z + beta p (one FMA per row).
+template <bool HOST, class T>
+__global__ void __launch_bounds__(kThreads, 4) k3_kernel(Args<T> a, double beta_host) {
+  using VT = typename V16<T>::type;
+  constexpr int E = V16<T>::E;
+  if (!HOST && read_done(a.st)) return;
+  const T beta = HOST ? (T)beta_host : (T)a.st->beta;
+  const int64_t n = a.n, nv = n / E, stride = (int64_t)gridDim.x * blockDim.x;
+  VT* pv = reinterpret_cast<VT*>(a.p);
+  const VT* zv = reinterpret_cast<const VT*>(a.z);
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nv; i0 += kAypxV * stride) {
+    VT pp[kAypxV], zz[kAypxV];
+#pragma unroll
+    for (int u = 0; u < kAypxV; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < nv) {
+        pp[u] = pv[i];
+        zz[u] = dev::ld_stream2(zv + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kAypxV; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < nv) {
+        T* pe = reinterpret_cast<T*>(&pp[u]);
+        const T* ze = reinterpret_cast<const T*>(&zz[u]);
+#pragma unroll
+        for (int e = 0; e < E; ++e) pe[e] = fma(beta, pe[e], ze[e]);
+        pv[i] = pp[u];
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int64_t i = nv * E; i < n; ++i) a.p[i] = fma(beta, a.p[i], a.z[i]);
+}
+
+template <class K>
+int occupancy_grid(K kernel, int sms, int64_t want) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int64_t g = (int64_t)per_sm * sms;
+  if (want < g) g = want;
+  if (g > dev::kMaxPartials) g = dev::kMaxPartials;
+  return g < 1 ? 1 : (int)g;
+}
+
+template <bool HOST, class T>
+apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
+  switch (c.u) {
+    case 4: k1_kernel<4, HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+    case 6: k1_kernel<6, HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+    default: k1_kernel<8, HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+  }
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+}  // namespace
+
+template <class T>
+void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
+  const double avg = c.n ? (double)nnz / c.n : 1.0;
+  c.u = avg <= 4.0 ? 4 : avg <= 6.0 ? 6 : 8;
+  const int64_t tiles = ((int64_t)c.n + 31) / 32;
+  const int64_t spmv_blocks = (tiles + kThreads / 32 - 1) / (kThreads / 32);
+  const int64_t vec_blocks = (((int64_t)c.n / V16<T>::E) + (int64_t)kThreads * kUpdV - 1) / ((int64_t)kThreads * kUpdV);
+  void* k1 = c.u == 4 ? (void*)k1_kernel<4, false, T> : c.u == 6 ? (void*)k1_kernel<6, false, T> : (void*)k1_kernel<8, false, T>;
+  c.grid_spmv = occupancy_grid(k1, sms, spmv_blocks);
+  c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
+}
+
+template <class T>
+apcg_status core_k1(const CgCore<T>& c, T* x, cudaStream_t s, bool host) {
+  const Args<T> a = make_args(c, x);
+  return host ? k1_dispatch<true>(c, a, s) : k1_dispatch<false>(c, a, s);
+}
+
+template <class T>
+apcg_status core_k2(const CgCore<T>& c, T* x, cudaStream_t s, bool host, double alpha,
+                    cudaGraphConditionalHandle cond, int use_cond) {
+  const Args<T> a = make_args(c, x);
+  if (host)
+    k2_kernel<true, T><<<c.grid_vec, kThreads, 0, s>>>(a, alpha, cond, use_cond);
+  else
+    k2_kernel<false, T><<<c.grid_vec, kThreads, 0, s>>>(a, alpha, cond, use_cond);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+template <class T>
+apcg_status core_k3(const CgCore<T>& c, T* x, cudaStream_t s, bool host, double beta) {
+  const Args<T> a = make_args(c, x);
+  if (host)
+    k3_kernel<true, T><<<c.grid_vec, kThreads, 0, s>>>(a, beta);
+  else
+    k3_kernel<false, T><<<c.grid_vec, kThreads, 0, s>>>(a, beta);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+template <class T>
+void core_release_graph(CgCore<T>& c) {
+  if (c.exec) cudaGraphExecDestroy(c.exec);
+  if (c.graph) cudaGraphDestroy(c.graph);
+  c.exec = nullptr;
+  c.graph = nullptr;
+  c.graph_x = nullptr;
+}
+
+template <class T>
+apcg_status core_build_graph(CgCore<T>& c, T* x, cudaStream_t upload) {
+  if (c.exec && c.graph_x == x) return APCG_OK;
+  core_release_graph(c);
+  if (!c.cap_stream) APCG_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  APCG_CUDA(cudaGraphCreate(&g, 0));
+  c.graph = g;
+  cudaGraphConditionalHandle h;
+  APCG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  APCG_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  APCG_CUDA(cudaStreamBeginCaptureToGraph(c.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  apcg_status st = APCG_OK;
+  for (int j = 0; j < c.k && st == APCG_OK; ++j) {
+    st = core_k1(c, x, c.cap_stream, false);
+    if (st == APCG_OK) st = core_k2(c, x, c.cap_stream, false, 0.0, h, j == c.k - 1 ? 1 : 0);
+    if (st == APCG_OK) st = core_k3(c, x, c.cap_stream, false, 0.0);
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c.cap_stream, &captured);
+  if (st != APCG_OK) return st;
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  APCG_CUDA(cudaGraphInstantiate(&c.exec, g, 0));
+  APCG_CUDA(cudaGraphUpload(c.exec, upload));
+  c.graph_x = x;
+  return APCG_OK;
+}
+
+apcg_status core_setup_f64(const CgCore<double>& c, const double* b, double* x, double rtol, double atol,
+                           cudaStream_t s) {
+  const Args<double> a = make_args(c, x);
+  switch (c.u) {
+    case 4: setup_kernel<4><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+    case 6: setup_kernel<6><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+    default: setup_kernel<8><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+  }
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+template void core_configure<double>(CgCore<double>&, int64_t, int);
+template void core_configure<float>(CgCore<float>&, int64_t, int);
+template apcg_status core_k1<double>(const CgCore<double>&, double*, cudaStream_t, bool);
+template apcg_status core_k1<float>(const CgCore<float>&, float*, cudaStream_t, bool);
+template apcg_status core_k2<double>(const CgCore<double>&, double*, cudaStream_t, bool, double,
+                                     cudaGraphConditionalHandle, int);
+template apcg_status core_k2<float>(const CgCore<float>&, float*, cudaStream_t, bool, double,
+                                    cudaGraphConditionalHandle, int);
+template apcg_status core_k3<double>(const CgCore<double>&, double*, cudaStream_t, bool, double);
+template apcg_status core_k3<float>(const CgCore<float>&, float*, cudaStream_t, bool, double);
+template apcg_status core_build_graph<double>(CgCore<double>&, double*, cudaStream_t);
+template apcg_status core_build_graph<float>(CgCore<float>&, float*, cudaStream_t);
+template void core_release_graph<double>(CgCore<double>&);
+template void core_release_graph<float>(CgCore<float>&);
+
+}  // namespace apcg

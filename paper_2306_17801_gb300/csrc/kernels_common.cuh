@@ -13,72 +13,13 @@ namespace dev {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxPartials = 4096;  // upper bound on the grid of any reducing kernel
 
-// L2 eviction-priority policies.  A float64 CG iteration streams the CSR
-// arrays (12 bytes per nonzero) once and touches six vectors several times;
-// the vectors (about 100 MB at n = 2M) fit in GB300's 126 MB L2 if the CSR
-// stream does not displace them.  Matrix loads therefore carry an evict-first
-// policy and vector loads/stores an evict-last policy.
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-// Read-only, not allocated in L1, with an L2 policy.
-__device__ __forceinline__ double ld_nc_hint(const double* a, uint64_t pol) {
-  double v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ float ld_nc_hint(const float* a, uint64_t pol) {
-  float v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ int32_t ld_nc_hint(const int32_t* a, uint64_t pol) {
-  int32_t v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
-  return v;
-}
-// Read-only through L1, with an L2 policy (gathered vector entries).
-__device__ __forceinline__ double ld_ro_hint(const double* a, uint64_t pol) {
-  double v;
-  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ float ld_ro_hint(const float* a, uint64_t pol) {
-  float v;
-  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
-  return v;
-}
-// 16-byte vector accesses with an L2 policy (coherent: the vector may be written by this kernel).
-__device__ __forceinline__ double2 ld2_hint(const double2* a, uint64_t pol) {
-  double2 v;
-  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol) : "memory");
-  return v;
-}
-__device__ __forceinline__ double2 ld2_nc_hint(const double2* a, uint64_t pol) {
-  double2 v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ void st2_hint(double2* a, double2 v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void st_hint(double* a, double v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
-}
-
 // Streaming loads (evict-first): matrix values and column indices are read
 // once per sweep and should not displace the vectors from L2.
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ double2 ld_stream2(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream2(const float4* p) { return __ldcs(p); }
 // Read-only path for gathered vector entries (L1-allocating).
 template <class T>
 __device__ __forceinline__ T ld_ro(const T* p) {

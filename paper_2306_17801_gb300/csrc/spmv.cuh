@@ -12,9 +12,9 @@
 // gathers of x -- so that every lane keeps 2U independent requests in
 // flight, and the row bounds of the warp's next tile are fetched while the
 // current tile is processed.  The x gathers go through the read-only L1 path;
-// col/val are loaded with an evict-first hint so that they stream through L2
-// without displacing the vectors.  A row's result does not depend on the
-// tile shape: its terms are always fused in storage order.
+// col/val are loaded with the streaming (evict-first) cache operator.  A row's
+// result does not depend on the tile shape: its terms are always fused in
+// storage order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,12 +33,14 @@ struct SpmvSmem {
 };
 
 // Apply `epi(row, value, x_own)` for every row handled by this warp, where
-// x_own = x[row] (square matrices only: pass own_x = false otherwise, x_own
-// is then 0).  Warps of the whole grid take 32-row tiles in a grid-stride
-// loop.  All 32 lanes must call this function together.
-template <int U, bool OWN_X, class T, class Epi>
+// x_own = x[row] (square matrices only: pass OWN_X = false otherwise, x_own
+// is then 0).  Matrix values have type TV and are widened to the vector type
+// T, in which the row sums are formed (float32 values times float64 x is
+// exact widening).  Warps of the whole grid take 32-row tiles in a
+// grid-stride loop.  All 32 lanes must call this function together.
+template <int U, bool OWN_X, class T, class TV = T, class Epi>
 __device__ __forceinline__ void spmv_warp_tiles(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                                const T* __restrict__ val, const T* __restrict__ x, int32_t nrows,
+                                                const TV* __restrict__ val, const T* __restrict__ x, int32_t nrows,
                                                 T* __restrict__ wbuf, Epi epi) {
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
@@ -52,33 +54,33 @@ __device__ __forceinline__ void spmv_warp_tiles(const int32_t* __restrict__ rowp
     rs = __ldg(rowptr + rlo);
     re = __ldg(rowptr + rhi);
   };
-  const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
   int32_t rs_next = 0, re_next = 0;
   if (gwarp < ntiles) bounds(gwarp, rs_next, re_next);
   for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
     const int32_t rs = rs_next, re = re_next;
     const int32_t row = (int32_t)(tile * 32 + lane);
     T x_own = T(0);
-    if (OWN_X && row < nrows) x_own = ld_ro_hint(x + row, pol_keep);
+    if (OWN_X && row < nrows) x_own = ld_ro(x + row);
     if (tile + nwarps < ntiles) bounds(tile + nwarps, rs_next, re_next);
     const int32_t base = __shfl_sync(kFull, rs, 0);
     const int32_t end = __shfl_sync(kFull, re, 31);
     T acc = T(0);
     for (int32_t c = base; c < end; c += 32 * U) {
       int32_t j[U];
-      T a[U], xv[U];
+      TV a[U];
+      T xv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int32_t e = c + u * 32 + lane;
         const bool ok = e < end;
-        j[u] = ok ? ld_nc_hint(col + e, pol_stream) : -1;
-        a[u] = ok ? ld_nc_hint(val + e, pol_stream) : T(0);
+        j[u] = ok ? ld_stream(col + e) : -1;
+        a[u] = ok ? ld_stream(val + e) : TV(0);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) xv[u] = j[u] >= 0 ? ld_ro_hint(x + j[u], pol_keep) : T(0);
+      for (int u = 0; u < U; ++u) xv[u] = j[u] >= 0 ? ld_ro(x + j[u]) : T(0);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        wbuf[u * 32 + lane] = a[u];
+        wbuf[u * 32 + lane] = (T)a[u];
         wbuf[32 * U + u * 32 + lane] = xv[u];
       }
       __syncwarp();
