@@ -21,10 +21,10 @@ namespace apcg {
 apcg_status set_error(apcg_status st, const char* fmt, ...);
 apcg_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
-#define APCG_CUDA(call)                                                  \
+#define APCG_CUDA(...)                                                   \
   do {                                                                   \
-    cudaError_t e_ = (call);                                             \
-    if (e_ != cudaSuccess) return ::apcg::cuda_error(e_, #call, __FILE__, __LINE__); \
+    cudaError_t e_ = (__VA_ARGS__);                                      \
+    if (e_ != cudaSuccess) return ::apcg::cuda_error(e_, #__VA_ARGS__, __FILE__, __LINE__); \
   } while (0)
 
 #define APCG_CHECK(cond, ...)                                           \
@@ -32,9 +32,9 @@ apcg_status cuda_error(cudaError_t e, const char* what, const char* file, int li
     if (!(cond)) return ::apcg::set_error(APCG_ERR_INVALID_ARG, __VA_ARGS__); \
   } while (0)
 
-#define APCG_TRY(expr)               \
+#define APCG_TRY(...)                \
   do {                               \
-    apcg_status s_ = (expr);         \
+    apcg_status s_ = (__VA_ARGS__);  \
     if (s_ != APCG_OK) return s_;    \
   } while (0)
 

@@ -25,6 +25,7 @@
 #include "cg_internal.hpp"
 #include "cluster_cg.hpp"
 #include "kernels_common.cuh"
+#include "sell.hpp"
 
 struct apcg_cg_plan_s {
   apcg_ctx ctx = nullptr;
@@ -159,9 +160,9 @@ apcg_status enqueue_persistent(apcg_cg_plan P, const double* b, double* x) {
   cudaStream_t s = P->ctx->stream;
   const CgCore<double>& c = P->core;
   ClusterArgs ca{};
-  ca.rowptr = c.rowptr;
-  ca.col = c.col;
-  ca.val = c.val;
+  ca.rowptr = P->A.rowptr;
+  ca.col = P->A.col;
+  ca.val = static_cast<const double*>(P->A.val);
   ca.dinv = c.dinv;
   ca.b = b;
   ca.x = x;
@@ -260,9 +261,6 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   c.k = o.check_every;
   c.max_it = o.max_it > 0 ? o.max_it : (c.n > 0 ? 10 * c.n : 10);
   c.hist_len = o.history_len;
-  c.rowptr = A->rowptr;
-  c.col = A->col;
-  c.val = static_cast<const double*>(A->val);
   P->mode = o.mode;
   if (o.mode == APCG_MODE_PERSISTENT || o.mode == APCG_MODE_AUTO) {
     P->shape = c.n <= kPersistentMaxRows ? default_cluster_shape(c.n) : ClusterShape{};
@@ -277,6 +275,10 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
     }
   }
   core_configure(c, A->nnz, ctx_num_sms(ctx));
+  // The iteration kernels read a sliced-ELL copy of A (sell.cuh); the cluster kernel reads the CSR itself.
+  SellLayout L;
+  const bool need_sell = P->mode != APCG_MODE_PERSISTENT;
+  if (need_sell) APCG_TRY(sell_layout(ctx->stream, c.n, A->rowptr, &L));
   // Workspace: dinv, r, p, w, z, partials, state, histories, cluster bookkeeping (one stream-ordered block).
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(double) * (size_t)(c.n > 0 ? c.n : 1));
@@ -284,7 +286,10 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   const size_t nst = up(sizeof(CgState));
   const size_t nh = up(sizeof(double) * (size_t)(c.hist_len > 0 ? c.hist_len : 1));
   const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
-  const size_t total = 5 * nv + npart + nst + 2 * nh + nsysb;
+  const size_t nsell = need_sell ? up(sizeof(int32_t) * ((size_t)L.nslices + 1)) + up(sizeof(int32_t) * (size_t)L.padded) +
+                                       up(sizeof(double) * (size_t)L.padded)
+                                 : 0;
+  const size_t total = 5 * nv + npart + nst + 2 * nh + nsysb + nsell;
   char* ws = nullptr;
   APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
   P->ws = ws;
@@ -302,6 +307,23 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   P->sres = reinterpret_cast<SysResult*>(tail + sizeof(SysDesc));
   P->next = reinterpret_cast<unsigned int*>(tail + sizeof(SysDesc) + sizeof(SysResult));
   APCG_CUDA(cudaMemsetAsync(ws + 5 * nv, 0, npart + nst + 2 * nh + nsysb, ctx->stream));
+  if (need_sell) {
+    char* q = tail + nsysb;
+    int32_t* sptr = reinterpret_cast<int32_t*>(q);
+    q += up(sizeof(int32_t) * ((size_t)L.nslices + 1));
+    int32_t* scol = reinterpret_cast<int32_t*>(q);
+    q += up(sizeof(int32_t) * (size_t)L.padded);
+    double* sval = reinterpret_cast<double*>(q);
+    APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice,
+                              ctx->stream));
+    APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
+                                       scol, sval));
+    c.A.n = c.n;
+    c.A.nslices = L.nslices;
+    c.A.sptr = sptr;
+    c.A.col = scol;
+    c.A.val = sval;
+  }
   SysDesc d0{};
   d0.row0 = 0;
   d0.n = c.n;

@@ -31,7 +31,7 @@
 
 #include "cg_core.hpp"
 #include "kernels_common.cuh"
-#include "spmv.cuh"
+#include "sell.cuh"
 
 namespace apcg {
 namespace {
@@ -56,9 +56,7 @@ struct V16<float> {
 
 template <class T>
 struct Args {
-  const int32_t* __restrict__ rowptr;
-  const int32_t* __restrict__ col;
-  const T* __restrict__ val;
+  dev::SellView<T> A;  // the plan's sliced-ELL copy of the matrix
   int32_t n;
   const T* __restrict__ dinv;
   T* x;
@@ -75,9 +73,7 @@ struct Args {
 template <class T>
 Args<T> make_args(const CgCore<T>& c, T* x) {
   Args<T> a;
-  a.rowptr = c.rowptr;
-  a.col = c.col;
-  a.val = c.val;
+  a.A = c.A;
   a.n = c.n;
   a.dinv = c.dinv;
   a.x = x;
@@ -95,14 +91,11 @@ Args<T> make_args(const CgCore<T>& c, T* x) {
 __device__ __forceinline__ int32_t read_done(const CgState* st) { return *(volatile const int32_t*)&st->done; }
 
 // r = b - A x0, z = D^-1 r, p = z; rho = (r,z), rr = (r,r), bb = (b,b) (float64 solve).
-template <int U>
 __global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const double* __restrict__ b, double rtol,
                                                          double atol, int32_t max_it, int32_t k, int32_t hist_len) {
-  __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
   __shared__ double red[3 * kThreads];
   double v[3] = {0.0, 0.0, 0.0};
-  dev::spmv_warp_tiles<U, false, double>(a.rowptr, a.col, a.val, a.x, a.n, sm[threadIdx.x >> 5].buf,
-                                         [&](int32_t i, double ax, double) {
+  dev::sell_spmv<false, double>(a.A, a.x, [&](int32_t i, double ax, double) {
                                            const double bi = __ldg(b + i);
                                            const double ri = bi - ax;
                                            const double zi = __ldg(a.dinv + i) * ri;
@@ -131,14 +124,12 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const d
 }
 
 // K1
-template <int U, bool HOST, class T>
+template <bool HOST, class T>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   if (!HOST && read_done(a.st)) return;
-  __shared__ dev::SpmvSmem<U, T> sm[kThreads / 32];
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
-  dev::spmv_warp_tiles<U, true, T>(a.rowptr, a.col, a.val, a.p, a.n, sm[threadIdx.x >> 5].buf,
-                                   [&](int32_t i, T s, T p_i) {
+  dev::sell_spmv<true, T>(a.A, a.p, [&](int32_t i, T s, T p_i) {
                                      a.w[i] = s;
                                      v[0] = fma(p_i, s, v[0]);
                                    });
@@ -338,11 +329,7 @@ int occupancy_grid(K kernel, int sms, int64_t want) {
 
 template <bool HOST, class T>
 apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
-  switch (c.u) {
-    case 4: k1_kernel<4, HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
-    case 6: k1_kernel<6, HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
-    default: k1_kernel<8, HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
-  }
+  k1_kernel<HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -351,13 +338,11 @@ apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
 
 template <class T>
 void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
-  const double avg = c.n ? (double)nnz / c.n : 1.0;
-  c.u = avg <= 4.0 ? 4 : avg <= 6.0 ? 6 : 8;
-  const int64_t tiles = ((int64_t)c.n + 31) / 32;
-  const int64_t spmv_blocks = (tiles + kThreads / 32 - 1) / (kThreads / 32);
+  (void)nnz;
+  const int64_t slices = ((int64_t)c.n + 31) / 32;
+  const int64_t spmv_blocks = (slices + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t vec_blocks = (((int64_t)c.n / V16<T>::E) + (int64_t)kThreads * kUpdV - 1) / ((int64_t)kThreads * kUpdV);
-  void* k1 = c.u == 4 ? (void*)k1_kernel<4, false, T> : c.u == 6 ? (void*)k1_kernel<6, false, T> : (void*)k1_kernel<8, false, T>;
-  c.grid_spmv = occupancy_grid(k1, sms, spmv_blocks);
+  c.grid_spmv = occupancy_grid((void*)k1_kernel<false, T>, sms, spmv_blocks);
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
 }
 
@@ -437,11 +422,7 @@ apcg_status core_build_graph(CgCore<T>& c, T* x, cudaStream_t upload) {
 apcg_status core_setup_f64(const CgCore<double>& c, const double* b, double* x, double rtol, double atol,
                            cudaStream_t s) {
   const Args<double> a = make_args(c, x);
-  switch (c.u) {
-    case 4: setup_kernel<4><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
-    case 6: setup_kernel<6><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
-    default: setup_kernel<8><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
-  }
+  setup_kernel<<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }

@@ -10,6 +10,7 @@
 
 #include "apcg_internal.hpp"
 #include "cg_internal.hpp"
+#include "sell.cuh"
 
 namespace apcg {
 
@@ -19,11 +20,8 @@ struct CgCore {
   int32_t k = 1;          // convergence test every k iterations
   int32_t max_it = 0;
   int32_t hist_len = 0;
-  int u = 8;              // SpMV chunk: 32*u nonzeros per warp pass
   int grid_spmv = 1, grid_vec = 1;
-  const int32_t* rowptr = nullptr;
-  const int32_t* col = nullptr;
-  const T* val = nullptr;
+  dev::SellView<T> A;     // sliced-ELL copy of the matrix (values in T)
   T* dinv = nullptr;
   T* r = nullptr;
   T* p = nullptr;
@@ -39,7 +37,7 @@ struct CgCore {
   T* graph_x = nullptr;
 };
 
-// Choose the SpMV chunk and persistent grids for n rows and nnz nonzeros.
+// Choose the persistent grids for n rows (nnz is informational).
 template <class T>
 void core_configure(CgCore<T>& c, int64_t nnz, int sms);
 

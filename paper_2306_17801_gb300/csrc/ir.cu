@@ -9,11 +9,13 @@
 //   r = b - A x (float64);  stop if ||r|| <= max(rtol ||b||, atol)
 //   inner: float32 PCG on A32 d = (float) r from d = 0 to rtol_inner ||(float) r||
 //   x += (double) d
-// The outer residual kernel also sets up the inner solve (r32, z = D32^-1 r32,
-// p = z, d = 0, rho, (r,r) and the tolerance), so each correction is one
-// residual kernel, one inner graph launch (k iterations per body of a
+// The outer residual kernel also sets up the inner solve, so each correction
+// is one residual kernel, one inner graph launch (k iterations per body of a
 // conditional while node, the float32 instance of the CG core) and one update
-// kernel; the host reads two norms once per correction.
+// kernel; the host reads two norms once per correction.  Both the outer and
+// the inner SpMV read the plan's sliced-ELL copy of the matrix (one column
+// array; float64 values for the outer residual unless the float32 values are
+// exact copies, float32 values for the inner solve).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,145 +26,28 @@
 #include "apcg_internal.hpp"
 #include "cg_core.hpp"
 #include "cg_internal.hpp"
-#include "kernels_common.cuh"
-#include "spmv.cuh"
+#include "ir_kernels.cuh"
+#include "sell.hpp"
 
-namespace apcg {
-namespace {
-
-constexpr int kThreads = 256;
-
-struct IrState {
-  double rnorm2;  // ||b - A x||^2 of the latest outer residual
-  double bnorm2;  // ||b||^2
-  unsigned int ticket;
-  int32_t pad;
-};
-
-// val32 = round-to-nearest float32 of val64.
-__global__ void to_f32_kernel(const double* __restrict__ v64, float* __restrict__ v32, int64_t n) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v32[i] = (float)v64[i];
-}
-
-// dinv32 = 1 / diag(A32) in float32; flags a missing, zero or non-finite entry.
-__global__ void jacobi32_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                const float* __restrict__ val, int32_t n, float* __restrict__ dinv, int32_t* err) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    float d = 0.0f;
-    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
-      if (col[e] == (int32_t)i) d += val[e];
-    const bool bad = !(d != 0.0f) || !isfinite(d);
-    if (bad) atomicOr(err, kDevErrBadDiagonal);
-    dinv[i] = bad ? 0.0f : 1.0f / d;
-  }
-}
-
-struct ResidualArgs {
-  const int32_t* rowptr;
-  const int32_t* col;
-  int32_t n;
-  const double* b;
-  const double* x;
-  float* r32;
-  float* p32;
-  float* d32;
-  const float* dinv32;
-  IrState* ost;
-  double* opartials;  // [2 * kMaxPartials]
-  CgState* ist;       // inner state block
-  float* ipartials;   // [2 * kMaxPartials] (the inner core's partials)
-  float rtol_inner;
-  int32_t max_inner, inner_k;
-};
-
-// r = b - A x in float64 (values TV widened to double), then the inner set-up.
-template <int U, class TV>
-__global__ void __launch_bounds__(kThreads) residual_kernel(ResidualArgs a, const TV* __restrict__ val) {
-  __shared__ dev::SpmvSmem<U, double> sm[kThreads / 32];
-  __shared__ double red64[2 * kThreads];
-  __shared__ float red32[2 * kThreads];
-  double v64[2] = {0.0, 0.0};
-  float v32[2] = {0.0f, 0.0f};
-  dev::spmv_warp_tiles<U, false, double, TV>(a.rowptr, a.col, val, a.x, a.n, sm[threadIdx.x >> 5].buf,
-                                             [&](int32_t i, double ax, double) {
-                                               const double bi = __ldg(a.b + i);
-                                               const double ri = bi - ax;
-                                               v64[0] = fma(ri, ri, v64[0]);
-                                               v64[1] = fma(bi, bi, v64[1]);
-                                               const float rf = (float)ri;
-                                               const float zf = __ldg(a.dinv32 + i) * rf;
-                                               a.r32[i] = rf;
-                                               a.p32[i] = zf;
-                                               a.d32[i] = 0.0f;
-                                               v32[0] = fmaf(rf, zf, v32[0]);
-                                               v32[1] = fmaf(rf, rf, v32[1]);
-                                             });
-  double t64[2];
-  if (dev::grid_sum_last<2>(v64, a.opartials, &a.ost->ticket, red64, t64) && threadIdx.x == 0) {
-    a.ost->rnorm2 = t64[0];
-    a.ost->bnorm2 = t64[1];
-  }
-  float t32[2];
-  if (dev::grid_sum_last<2>(v32, a.ipartials, &a.ist->ticket, red32, t32) && threadIdx.x == 0) {
-    CgState* st = a.ist;
-    st->rho = t32[0];
-    st->rr = t32[1];
-    st->bnorm2 = t32[1];
-    const float tol = a.rtol_inner * sqrtf(t32[1]);
-    st->tol = tol;
-    st->iter = 0;
-    st->max_it = a.max_inner;
-    st->check_every = a.inner_k;
-    st->hist_len = 0;
-    st->body_runs = 0;
-    st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
-    st->done = (sqrtf(t32[1]) <= tol) ? kDoneConverged : 0;
-  }
-}
-
-// x += (double) d.
-__global__ void __launch_bounds__(kThreads) update_kernel(double* __restrict__ x, const float* __restrict__ d,
-                                                          int64_t n) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n4 = n / 4;
-  double2* x2 = reinterpret_cast<double2*>(x);
-  const float4* d4 = reinterpret_cast<const float4*>(d);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-    const float4 dd = __ldg(d4 + i);
-    double2 a = x2[2 * i], b = x2[2 * i + 1];
-    a.x += (double)dd.x;
-    a.y += (double)dd.y;
-    b.x += (double)dd.z;
-    b.y += (double)dd.w;
-    x2[2 * i] = a;
-    x2[2 * i + 1] = b;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0)
-    for (int64_t i = n4 * 4; i < n; ++i) x[i] += (double)d[i];
-}
-
-}  // namespace
-}  // namespace apcg
+using apcg::ir::IrState;
+using apcg::ir::kThreads;
 
 struct apcg_ir_plan_s {
   apcg_ctx ctx = nullptr;
   apcg_ir_opts opts{};
   int32_t n = 0;
   int64_t nnz = 0;
-  const int32_t* rowptr = nullptr;
-  const int32_t* col = nullptr;
-  const double* val64 = nullptr;  // outer residual values (or nullptr: widen val32)
-  const float* val32 = nullptr;   // inner values (the caller's or the plan's copy)
   apcg_id id_a64 = 0, id_a32 = 0, id = 0;
-  apcg::CgCore<float> core;       // inner solver; its x is d32
+  apcg::dev::SellView<double> A64;  // outer residual values (nslices == 0 when absent)
+  apcg::dev::SellView<float> A32;   // inner values (also the outer ones when A64 is absent)
+  apcg::CgCore<float> core;         // inner solver; its x is d32
   float* d32 = nullptr;
-  apcg::IrState* ost = nullptr;
+  IrState* ost = nullptr;
   double* opartials = nullptr;
   char* ws = nullptr;
-  int grid_res = 1, grid_upd = 1, u = 8;
-  void* host_state = nullptr;     // pinned: IrState followed by CgState
+  int grid_res = 1, grid_upd = 1;
+  bool outer64 = false;
+  void* host_state = nullptr;  // pinned: IrState followed by CgState
 };
 
 namespace apcg {
@@ -187,9 +72,7 @@ void ir_destroy(apcg_ir_plan P) {
 }
 
 apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cudaStream_t s) {
-  ResidualArgs a;
-  a.rowptr = P->rowptr;
-  a.col = P->col;
+  ir::ResidualArgs a;
   a.n = P->n;
   a.b = b;
   a.x = x;
@@ -204,20 +87,10 @@ apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cu
   a.rtol_inner = P->opts.rtol_inner;
   a.max_inner = P->core.max_it;
   a.inner_k = P->core.k;
-  const int g = P->grid_res;
-  if (P->val64) {
-    switch (P->u) {
-      case 4: residual_kernel<4, double><<<g, kThreads, 0, s>>>(a, P->val64); break;
-      case 6: residual_kernel<6, double><<<g, kThreads, 0, s>>>(a, P->val64); break;
-      default: residual_kernel<8, double><<<g, kThreads, 0, s>>>(a, P->val64); break;
-    }
-  } else {
-    switch (P->u) {
-      case 4: residual_kernel<4, float><<<g, kThreads, 0, s>>>(a, P->val32); break;
-      case 6: residual_kernel<6, float><<<g, kThreads, 0, s>>>(a, P->val32); break;
-      default: residual_kernel<8, float><<<g, kThreads, 0, s>>>(a, P->val32); break;
-    }
-  }
+  if (P->outer64)
+    ir::residual_kernel<double><<<P->grid_res, kThreads, 0, s>>>(a, P->A64);
+  else
+    ir::residual_kernel<float><<<P->grid_res, kThreads, 0, s>>>(a, P->A32);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -267,37 +140,44 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   P->opts = o;
   P->n = S.nrows;
   P->nnz = S.nnz;
-  P->rowptr = S.rowptr;
-  P->col = S.col;
-  P->val64 = A64 ? static_cast<const double*>(A64->val) : nullptr;
   P->id_a64 = A64 ? A64->id : 0;
   P->id_a32 = A32 ? A32->id : 0;
+  P->outer64 = A64 != nullptr;
   CgCore<float>& c = P->core;
   c.n = P->n;
   c.k = o.inner_check_every;
   c.max_it = o.max_inner;
   c.hist_len = 0;
-  c.rowptr = S.rowptr;
-  c.col = S.col;
   const int sms = ctx_num_sms(ctx);
   core_configure(c, S.nnz, sms);
-  P->u = c.u;
   P->grid_res = c.grid_spmv;
   P->grid_upd = std::max(1, std::min(sms * 8, (int)((P->n / 4 + kThreads - 1) / kThreads)));
-  // Workspace: val32 copy (if needed), dinv32, r, p, w, z, d (float), partials, states.
+  SellLayout L;
+  APCG_TRY(sell_layout(ctx->stream, P->n, S.rowptr, &L));
+  // Workspace: sliced-ELL (sptr, col, float32 values, float64 values if A64), dinv32, r, p, w, z, d,
+  // partials and states.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(float) * (size_t)(P->n > 0 ? P->n : 1));
-  const size_t nval = A32 ? 0 : up(sizeof(float) * (size_t)(P->nnz > 0 ? P->nnz : 1));
+  const size_t nsptr = up(sizeof(int32_t) * ((size_t)L.nslices + 1));
+  const size_t ncol = up(sizeof(int32_t) * (size_t)std::max<int64_t>(L.padded, 1));
+  const size_t nv32 = up(sizeof(float) * (size_t)std::max<int64_t>(L.padded, 1));
+  const size_t nv64 = A64 ? up(sizeof(double) * (size_t)std::max<int64_t>(L.padded, 1)) : 0;
   const size_t nip = up(sizeof(float) * dev::kMaxPartials * 3);
   const size_t nop = up(sizeof(double) * dev::kMaxPartials * 2);
   const size_t nst = up(sizeof(CgState)) + up(sizeof(IrState));
-  const size_t total = nval + 6 * nv + nip + nop + nst;
+  const size_t total = nsptr + ncol + nv32 + nv64 + 6 * nv + nip + nop + nst;
   char* ws = nullptr;
   APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
   P->ws = ws;
   char* q = ws;
-  float* v32own = nval ? reinterpret_cast<float*>(q) : nullptr;
-  q += nval;
+  int32_t* sptr = reinterpret_cast<int32_t*>(q);
+  q += nsptr;
+  int32_t* scol = reinterpret_cast<int32_t*>(q);
+  q += ncol;
+  float* sval32 = reinterpret_cast<float*>(q);
+  q += nv32;
+  double* sval64 = A64 ? reinterpret_cast<double*>(q) : nullptr;
+  q += nv64;
   c.dinv = reinterpret_cast<float*>(q);
   c.r = reinterpret_cast<float*>(q + nv);
   c.p = reinterpret_cast<float*>(q + 2 * nv);
@@ -319,20 +199,37 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   OpScope op(ctx);
   op.read(P->id_a64).read(P->id_a32).write(P->id);
   APCG_TRY(op.begin());
-  if (v32own) {
-    const int g = std::max(1, std::min(sms * 8, (int)((P->nnz + kThreads - 1) / kThreads)));
-    to_f32_kernel<<<g, kThreads, 0, ctx->stream>>>(P->val64, v32own, P->nnz);
-    APCG_CUDA(cudaGetLastError());
-    count_kernels(1);
-    P->val32 = v32own;
-  } else {
-    P->val32 = static_cast<const float*>(A32->val);
+  APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  if (A32)
+    APCG_TRY(sell_fill<float, float>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const float*>(A32->val),
+                                     scol, sval32));
+  else
+    APCG_TRY(sell_fill<double, float>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const double*>(A64->val),
+                                      scol, sval32));
+  if (A64)
+    APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const double*>(A64->val),
+                                       nullptr, sval64));
+  P->A32.n = P->A64.n = P->n;
+  P->A32.nslices = L.nslices;
+  P->A32.sptr = sptr;
+  P->A32.col = scol;
+  P->A32.val = sval32;
+  if (A64) {
+    P->A64.nslices = L.nslices;
+    P->A64.sptr = sptr;
+    P->A64.col = scol;
+    P->A64.val = sval64;
   }
-  c.val = P->val32;
+  c.A = P->A32;
   if (P->n > 0) {
     const int g = std::max(1, std::min(sms * 8, (int)((P->n + kThreads - 1) / kThreads)));
-    jacobi32_kernel<<<g, kThreads, 0, ctx->stream>>>(P->rowptr, P->col, P->val32, P->n, c.dinv,
-                                                      ctx->scratch.dev_error);
+    if (A32)
+      ir::jacobi32_kernel<float><<<g, kThreads, 0, ctx->stream>>>(S.rowptr, S.col, static_cast<const float*>(A32->val),
+                                                                  P->n, c.dinv, ctx->scratch.dev_error);
+    else
+      ir::jacobi32_kernel<double><<<g, kThreads, 0, ctx->stream>>>(
+          S.rowptr, S.col, static_cast<const double*>(A64->val), P->n, c.dinv, ctx->scratch.dev_error);
     APCG_CUDA(cudaGetLastError());
     count_kernels(1);
   }
@@ -399,7 +296,7 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
     }
     counters().graph_launches++;
     const int g = P->grid_upd;
-    update_kernel<<<g, kThreads, 0, s>>>(xp, P->d32, P->n);
+    ir::update_kernel<<<g, kThreads, 0, s>>>(xp, P->d32, P->n);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       st = cuda_error(e, "update launch", __FILE__, __LINE__);

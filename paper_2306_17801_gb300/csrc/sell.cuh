@@ -1,0 +1,86 @@
+// Sliced-ELL layout of a CSR matrix, and the SpMV over it.
+//
+// The plan converts the caller's CSR matrix once into slices of 32
+// consecutive rows stored column-major: entry k of row 32 s + l sits at
+// sptr[s] + 32 k + l, each slice padded to its longest row (padding: value 0,
+// column = the row itself, or 0 past the last row).  Row order is unchanged,
+// so vectors keep their layout.  Why: on GB300 a float64 FMA costs one warp
+// instruction on a pipe that retires two lanes per SM per cycle, so the SpMV
+// must keep all 32 lanes busy on every FMA.  In this layout lane l owns row
+// 32 s + l and loads its own entries with fully coalesced accesses; a slice of
+// rows with w entries costs exactly w FMA instructions, whatever w is (the
+// CSR warp tiles of spmv.cuh leave lanes idle when rows straddle chunks, as
+// 27-point rows do).  Stencil slices carry almost no padding.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels_common.cuh"
+
+namespace apcg {
+namespace dev {
+
+template <class TV>
+struct SellView {
+  int32_t n = 0;        // rows
+  int32_t nslices = 0;  // ceil(n / 32)
+  const int32_t* __restrict__ sptr = nullptr;  // [nslices + 1] entry offsets (multiples of 32)
+  const int32_t* __restrict__ col = nullptr;   // [sptr[nslices]]
+  const TV* __restrict__ val = nullptr;        // [sptr[nslices]]
+};
+
+// Apply epi(row, (A x)[row], x[row]) for every row; warps of the grid take
+// slices in a grid-stride loop.  Values TV are widened to T, the type of x
+// and of the row sums.  All 32 lanes must call this function together.
+template <bool OWN_X, class T, class TV, class Epi>
+__device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __restrict__ x, Epi epi) {
+  constexpr int G = 4;  // entries per lane loaded before their FMAs
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int32_t b_next = 0, e_next = 0;
+  if (gwarp < A.nslices) {
+    b_next = __ldg(A.sptr + gwarp);
+    e_next = __ldg(A.sptr + gwarp + 1);
+  }
+  for (int64_t s = gwarp; s < A.nslices; s += nwarps) {
+    const int32_t base = b_next, end = e_next;
+    if (s + nwarps < A.nslices) {
+      b_next = __ldg(A.sptr + s + nwarps);
+      e_next = __ldg(A.sptr + s + nwarps + 1);
+    }
+    const int32_t row = (int32_t)(s * 32 + lane);
+    T x_own = T(0);
+    if (OWN_X && row < A.n) x_own = ld_ro(x + row);
+    const int32_t* cp = A.col + base + lane;
+    const TV* vp = A.val + base + lane;
+    const int32_t width = (end - base) >> 5;
+    T acc = T(0);
+    int32_t k = 0;
+    for (; k + G <= width; k += G) {
+      int32_t j[G];
+      TV a[G];
+      T xv[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        j[g] = ld_stream(cp + 32 * (k + g));
+        a[g] = ld_stream(vp + 32 * (k + g));
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) xv[g] = ld_ro(x + j[g]);
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc = fma((T)a[g], xv[g], acc);
+    }
+    for (; k < width; ++k) {
+      const int32_t j = ld_stream(cp + 32 * k);
+      const TV a = ld_stream(vp + 32 * k);
+      acc = fma((T)a, ld_ro(x + j), acc);
+    }
+    if (row < A.n) epi(row, acc, x_own);
+  }
+}
+
+}  // namespace dev
+}  // namespace apcg

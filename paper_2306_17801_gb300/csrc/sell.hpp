@@ -1,0 +1,30 @@
+// Host side of the sliced-ELL conversion (see sell.cuh for the layout).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "apcg_internal.hpp"
+
+namespace apcg {
+
+struct SellLayout {
+  int32_t n = 0;
+  int32_t nslices = 0;
+  int64_t padded = 0;          // entries including padding (multiple of 32)
+  std::vector<int32_t> sptr;   // [nslices + 1]
+};
+
+// Slice offsets of a CSR matrix whose rowptr lives on the device (copied back once, blocks on s).
+apcg_status sell_layout(cudaStream_t s, int32_t n, const int32_t* rowptr_dev, SellLayout* out);
+
+// Scatter CSR rows into the slices: column indices (if scol != nullptr) and
+// values converted from TI to TO (if sval != nullptr).  d_sptr is the layout's
+// sptr on the device.
+template <class TI, class TO>
+apcg_status sell_fill(cudaStream_t s, const SellLayout& L, const int32_t* d_sptr, const int32_t* rowptr,
+                      const int32_t* col, const TI* val, int32_t* scol, TO* sval);
+
+}  // namespace apcg
