@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kUpdV = 2;   // 16-byte vectors per thread and array in K2
-constexpr int kAypxV = 2;  // 16-byte vectors per thread and array in K3
+constexpr int kAypxV = 4;  // 16-byte vectors per thread and array in K3
 
 // 16-byte vector of T: double2 or float4.
 template <class T>
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 4) k2_kernel(Args<T> a, double alpha
 
 // K3: p = z + beta p (one FMA per row).
 template <bool HOST, class T>
-__global__ void __launch_bounds__(kThreads) k3_kernel(Args<T> a, double beta_host) {
+__global__ void __launch_bounds__(kThreads, 4) k3_kernel(Args<T> a, double beta_host) {
   using VT = typename V16<T>::type;
   constexpr int E = V16<T>::E;
   if (!HOST && read_done(a.st)) return;
@@ -322,14 +322,9 @@ int occupancy_grid(K kernel, int sms, int64_t want) {
     per_sm = 1;
   }
   int64_t g = (int64_t)per_sm * sms;
+  if (want < g) g = want;
   if (g > dev::kMaxPartials) g = dev::kMaxPartials;
-  if (want <= g) return want < 1 ? 1 : (int)want;
-  // Persistent grid: the fewest passes that cover `want` blocks of work, and
-  // then the smallest grid with that many passes, so that no block does one
-  // pass more than another (a block that finishes early only waits at the
-  // reduction).
-  const int64_t passes = (want + g - 1) / g;
-  return (int)((want + passes - 1) / passes);
+  return g < 1 ? 1 : (int)g;
 }
 
 template <bool HOST, class T>
@@ -349,10 +344,6 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
   const int64_t vec_blocks = (((int64_t)c.n / V16<T>::E) + (int64_t)kThreads * kUpdV - 1) / ((int64_t)kThreads * kUpdV);
   c.grid_spmv = occupancy_grid((void*)k1_kernel<false, T>, sms, spmv_blocks);
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
-  // K3 has no reduction, so it needs no persistent grid: one pass per thread.
-  const int64_t nv = (int64_t)c.n / V16<T>::E;
-  const int64_t g3 = (nv + (int64_t)kThreads * kAypxV - 1) / ((int64_t)kThreads * kAypxV);
-  c.grid_aypx = (int)(g3 < 1 ? 1 : g3 > INT32_MAX ? INT32_MAX : g3);
 }
 
 template <class T>
@@ -377,9 +368,9 @@ template <class T>
 apcg_status core_k3(const CgCore<T>& c, T* x, cudaStream_t s, bool host, double beta) {
   const Args<T> a = make_args(c, x);
   if (host)
-    k3_kernel<true, T><<<c.grid_aypx, kThreads, 0, s>>>(a, beta);
+    k3_kernel<true, T><<<c.grid_vec, kThreads, 0, s>>>(a, beta);
   else
-    k3_kernel<false, T><<<c.grid_aypx, kThreads, 0, s>>>(a, beta);
+    k3_kernel<false, T><<<c.grid_vec, kThreads, 0, s>>>(a, beta);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }

@@ -20,7 +20,7 @@ struct CgCore {
   int32_t k = 1;          // convergence test every k iterations
   int32_t max_it = 0;
   int32_t hist_len = 0;
-  int grid_spmv = 1, grid_vec = 1, grid_aypx = 1;
+  int grid_spmv = 1, grid_vec = 1;
   dev::SellView<T> A;     // sliced-ELL copy of the matrix (values in T)
   T* dinv = nullptr;
   T* r = nullptr;
