@@ -37,7 +37,7 @@ namespace apcg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUpdV = 2;   // 16-byte vectors per thread and array in K2
+constexpr int kUpdV = 1;   // 16-byte vectors per thread and array in K2 (1 measured fastest)
 constexpr int kAypxV = 4;  // 16-byte vectors per thread and array in K3
 
 // 16-byte vector of T: double2 or float4.

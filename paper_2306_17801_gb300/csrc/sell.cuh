@@ -36,7 +36,7 @@ struct SellView {
 // and of the row sums.  All 32 lanes must call this function together.
 template <bool OWN_X, class T, class TV, class Epi>
 __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __restrict__ x, Epi epi) {
-  constexpr int G = 4;  // entries per lane loaded before their FMAs
+  constexpr int G = 8;  // entries per lane loaded before their FMAs (long rows)
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -58,25 +58,34 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
     const TV* vp = A.val + base + lane;
     const int32_t width = (end - base) >> 5;
     T acc = T(0);
-    int32_t k = 0;
-    for (; k + G <= width; k += G) {
-      int32_t j[G];
-      TV a[G];
-      T xv[G];
+    if (width >= G) {
+      // Long rows: groups of G entries per lane -- all column/value loads of a
+      // group, then its gathers, then its FMAs; the last group is predicated
+      // (the width is the same for the 32 lanes of a slice, so the predicate
+      // is uniform).
+      for (int32_t k = 0; k < width; k += G) {
+        int32_t j[G];
+        TV a[G];
+        T xv[G];
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        j[g] = ld_stream(cp + 32 * (k + g));
-        a[g] = ld_stream(vp + 32 * (k + g));
+        for (int g = 0; g < G; ++g) {
+          const bool ok = k + g < width;
+          j[g] = ok ? ld_stream(cp + 32 * (k + g)) : 0;
+          a[g] = ok ? ld_stream(vp + 32 * (k + g)) : TV(0);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) xv[g] = (k + g < width) ? ld_ro(x + j[g]) : T(0);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (k + g < width) acc = fma((T)a[g], xv[g], acc);
       }
-#pragma unroll
-      for (int g = 0; g < G; ++g) xv[g] = ld_ro(x + j[g]);
-#pragma unroll
-      for (int g = 0; g < G; ++g) acc = fma((T)a[g], xv[g], acc);
-    }
-    for (; k < width; ++k) {
-      const int32_t j = ld_stream(cp + 32 * k);
-      const TV a = ld_stream(vp + 32 * k);
-      acc = fma((T)a, ld_ro(x + j), acc);
+    } else {
+      // Short rows (5- and 7-point stencils): one entry at a time measured faster.
+      for (int32_t k = 0; k < width; ++k) {
+        const int32_t j = ld_stream(cp + 32 * k);
+        const TV a = ld_stream(vp + 32 * k);
+        acc = fma((T)a, ld_ro(x + j), acc);
+      }
     }
     if (row < A.n) epi(row, acc, x_own);
   }
