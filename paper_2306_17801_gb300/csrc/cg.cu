@@ -323,6 +323,8 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
     c.A.sptr = sptr;
     c.A.col = scol;
     c.A.val = sval;
+    c.A.long_rows = L.long_rows;
+    core_configure(c, A->nnz, ctx_num_sms(ctx));  // the SpMV kernel instance depends on the row length
   }
   SysDesc d0{};
   d0.row0 = 0;

@@ -91,11 +91,12 @@ Args<T> make_args(const CgCore<T>& c, T* x) {
 __device__ __forceinline__ int32_t read_done(const CgState* st) { return *(volatile const int32_t*)&st->done; }
 
 // r = b - A x0, z = D^-1 r, p = z; rho = (r,z), rr = (r,r), bb = (b,b) (float64 solve).
+template <bool LONG>
 __global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const double* __restrict__ b, double rtol,
                                                          double atol, int32_t max_it, int32_t k, int32_t hist_len) {
   __shared__ double red[3 * kThreads];
   double v[3] = {0.0, 0.0, 0.0};
-  dev::sell_spmv<false, double>(a.A, a.x, [&](int32_t i, double ax, double) {
+  dev::sell_spmv<false, LONG, double>(a.A, a.x, [&](int32_t i, double ax, double) {
                                            const double bi = __ldg(b + i);
                                            const double ri = bi - ax;
                                            const double zi = __ldg(a.dinv + i) * ri;
@@ -124,12 +125,12 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const d
 }
 
 // K1
-template <bool HOST, class T>
+template <bool HOST, bool LONG, class T>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   if (!HOST && read_done(a.st)) return;
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
-  dev::sell_spmv<true, T>(a.A, a.p, [&](int32_t i, T s, T p_i) {
+  dev::sell_spmv<true, LONG, T>(a.A, a.p, [&](int32_t i, T s, T p_i) {
                                      a.w[i] = s;
                                      v[0] = fma(p_i, s, v[0]);
                                    });
@@ -329,7 +330,10 @@ int occupancy_grid(K kernel, int sms, int64_t want) {
 
 template <bool HOST, class T>
 apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
-  k1_kernel<HOST, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
+  if (c.A.long_rows)
+    k1_kernel<HOST, true, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
+  else
+    k1_kernel<HOST, false, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -342,7 +346,8 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
   const int64_t slices = ((int64_t)c.n + 31) / 32;
   const int64_t spmv_blocks = (slices + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t vec_blocks = (((int64_t)c.n / V16<T>::E) + (int64_t)kThreads * kUpdV - 1) / ((int64_t)kThreads * kUpdV);
-  c.grid_spmv = occupancy_grid((void*)k1_kernel<false, T>, sms, spmv_blocks);
+  c.grid_spmv = occupancy_grid(c.A.long_rows ? (void*)k1_kernel<false, true, T> : (void*)k1_kernel<false, false, T>, sms,
+                               spmv_blocks);
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
 }
 
@@ -422,7 +427,10 @@ apcg_status core_build_graph(CgCore<T>& c, T* x, cudaStream_t upload) {
 apcg_status core_setup_f64(const CgCore<double>& c, const double* b, double* x, double rtol, double atol,
                            cudaStream_t s) {
   const Args<double> a = make_args(c, x);
-  setup_kernel<<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
+  if (c.A.long_rows)
+    setup_kernel<true><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
+  else
+    setup_kernel<false><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }

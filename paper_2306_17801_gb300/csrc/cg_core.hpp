@@ -37,7 +37,7 @@ struct CgCore {
   T* graph_x = nullptr;
 };
 
-// Choose the persistent grids for n rows (nnz is informational).
+// Choose the persistent grids for n rows (nnz is informational).  Call after c.A is set.
 template <class T>
 void core_configure(CgCore<T>& c, int64_t nnz, int sms);
 

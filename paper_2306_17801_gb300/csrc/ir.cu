@@ -87,10 +87,18 @@ apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cu
   a.rtol_inner = P->opts.rtol_inner;
   a.max_inner = P->core.max_it;
   a.inner_k = P->core.k;
-  if (P->outer64)
-    ir::residual_kernel<double><<<P->grid_res, kThreads, 0, s>>>(a, P->A64);
-  else
-    ir::residual_kernel<float><<<P->grid_res, kThreads, 0, s>>>(a, P->A32);
+  const bool lg = P->A32.long_rows != 0;
+  if (P->outer64) {
+    if (lg)
+      ir::residual_kernel<true, double><<<P->grid_res, kThreads, 0, s>>>(a, P->A64);
+    else
+      ir::residual_kernel<false, double><<<P->grid_res, kThreads, 0, s>>>(a, P->A64);
+  } else {
+    if (lg)
+      ir::residual_kernel<true, float><<<P->grid_res, kThreads, 0, s>>>(a, P->A32);
+    else
+      ir::residual_kernel<false, float><<<P->grid_res, kThreads, 0, s>>>(a, P->A32);
+  }
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -221,7 +229,10 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
     P->A64.col = scol;
     P->A64.val = sval64;
   }
+  P->A32.long_rows = P->A64.long_rows = L.long_rows;
   c.A = P->A32;
+  core_configure(c, S.nnz, sms);  // the SpMV kernel instance depends on the row length
+  P->grid_res = c.grid_spmv;
   if (P->n > 0) {
     const int g = std::max(1, std::min(sms * 8, (int)((P->n + kThreads - 1) / kThreads)));
     if (A32)

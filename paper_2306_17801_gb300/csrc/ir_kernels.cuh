@@ -58,13 +58,13 @@ struct ResidualArgs {
 // r = b - A x in float64 (values TV widened to double), ||r||^2 and ||b||^2 in
 // float64; then the inner set-up in float32: r32 = (float) r, p = z = D32^-1 r32,
 // d = 0, rho = (r32, z), (r32, r32) and the inner tolerance.
-template <class TV>
+template <bool LONG, class TV>
 __global__ void __launch_bounds__(kThreads) residual_kernel(ResidualArgs a, dev::SellView<TV> A) {
   __shared__ double red64[2 * kThreads];
   __shared__ float red32[2 * kThreads];
   double v64[2] = {0.0, 0.0};
   float v32[2] = {0.0f, 0.0f};
-  dev::sell_spmv<false, double>(A, a.x, [&](int32_t i, double ax, double) {
+  dev::sell_spmv<false, LONG, double>(A, a.x, [&](int32_t i, double ax, double) {
     const double bi = __ldg(a.b + i);
     const double ri = bi - ax;
     v64[0] = fma(ri, ri, v64[0]);

@@ -59,6 +59,7 @@ apcg_status sell_layout(cudaStream_t s, int32_t n, const int32_t* rowptr_dev, Se
   }
   out->sptr[out->nslices] = (int32_t)acc;
   out->padded = acc;
+  out->long_rows = out->nslices > 0 && acc >= 8LL * 32 * out->nslices;
   return APCG_OK;
 }
 

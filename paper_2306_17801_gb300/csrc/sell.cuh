@@ -29,12 +29,15 @@ struct SellView {
   const int32_t* __restrict__ sptr = nullptr;  // [nslices + 1] entry offsets (multiples of 32)
   const int32_t* __restrict__ col = nullptr;   // [sptr[nslices]]
   const TV* __restrict__ val = nullptr;        // [sptr[nslices]]
+  int32_t long_rows = 0;  // mean slice width >= 8: the kernels take the grouped path
 };
 
 // Apply epi(row, (A x)[row], x[row]) for every row; warps of the grid take
 // slices in a grid-stride loop.  Values TV are widened to T, the type of x
 // and of the row sums.  All 32 lanes must call this function together.
-template <bool OWN_X, class T, class TV, class Epi>
+// LONG selects the grouped path for long rows (it needs more registers, so
+// short-row matrices use a separate instance).
+template <bool OWN_X, bool LONG, class T, class TV, class Epi>
 __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __restrict__ x, Epi epi) {
   constexpr int G = 8;  // entries per lane loaded before their FMAs (long rows)
   const int lane = threadIdx.x & 31;
@@ -58,7 +61,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
     const TV* vp = A.val + base + lane;
     const int32_t width = (end - base) >> 5;
     T acc = T(0);
-    if (width >= G) {
+    if (LONG) {
       // Long rows: groups of G entries per lane -- all column/value loads of a
       // group, then its gathers, then its FMAs; the last group is predicated
       // (the width is the same for the 32 lanes of a slice, so the predicate
@@ -80,7 +83,8 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
           if (k + g < width) acc = fma((T)a[g], xv[g], acc);
       }
     } else {
-      // Short rows (5- and 7-point stencils): one entry at a time measured faster.
+      // Short rows (5- and 7-point stencils): one entry at a time (measured
+      // faster: fewer registers, more resident warps).
       for (int32_t k = 0; k < width; ++k) {
         const int32_t j = ld_stream(cp + 32 * k);
         const TV a = ld_stream(vp + 32 * k);
