@@ -280,7 +280,7 @@ def run_apcg(args, rank, world, local):
         ach = bytes_k1 / (ms_k[0] * 1e-3) / 1e9
         trec = _traffic_record()
         out["roofline"] = {
-            "kernel": "cg_spmv_dot_kernel (w = A p, (p,w), alpha)",
+            "kernel": "k1_kernel: SpMV w = A p with (p,w) and alpha (sliced-ELL, float64)",
             "bound": "hbm",
             "achieved": ach,
             "peak": peak,
