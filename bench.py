@@ -434,9 +434,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="only the set-up and 3 iterations, kernels launched one by one (for profilers)")
-    ap.add_argument("--config", choices=["c2", "c3", "c4"], default="c2",
-                    help="c2: the headline 128^3 workload (default); c3/c4: extra measurement lines")
-    ap.add_argument("--no-tune", action="store_true", help="c4: skip the batched autotuner")
+    ap.add_argument("--config", choices=["c2", "c3", "c4", "c5"], default="c2",
+                    help="c2: the headline 128^3 workload (default); c3/c4/c5: extra measurement lines")
+    ap.add_argument("--no-tune", action="store_true", help="c4/c5: skip the batched autotuner")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
@@ -457,7 +457,7 @@ def main():
         ncu_case()
         return
     if args.config != "c2":
-        {"c3": bench_c3, "c4": bench_c4}[args.config](args)
+        {"c3": bench_c3, "c4": bench_c4, "c5": bench_c5}[args.config](args)
         return
     run_apcg(args, rank, world, local)
 
@@ -598,6 +598,102 @@ def bench_c4(args):
     out["speedup_batched_vs_one_at_a_time"] = dt_seq / dt
     line = {"metric": "batched PCG solves/s at rtol 1e-8 (FP64)", "value": B.nsys / dt, "unit": "solves/s",
             "dtype": "f64", "data": "synthetic", **out}
+    print(json.dumps(line), flush=True)
+
+
+def bench_c5(args):
+    """4096 anisotropic 7-point systems (sides 8..32, float32-exact): batched float32-inner refinement
+    to rtol 1e-10 vs the batched float64 PCG and vs float64 solves one system at a time."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+    from synthetic import batch_aniso_7pt
+
+    V = C.c_void_p
+    dev = torch.device("cuda", 0)
+    apcg.load()
+    B = batch_aniso_7pt(4096, seed=0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rowptr, col, b = t(B.rowptr), t(B.col), t(B.b)
+    val32 = t(B.val.astype(np.float32))
+    val64 = t(B.val)
+    x = torch.zeros(B.n_total, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = apcg.ctx_create(stream)
+    nnz = int(B.rowptr[-1])
+    out = {"config": {"workload": f"4096 x anisotropic 3D 7-point, sides 8..32 ({B.n_total:,} rows, {nnz:,} nnz), "
+                                  "float32-exact values, rtol 1e-10"}}
+
+    def run(plan):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = apcg.batch_plan_solve(plan, b, x, B.nsys)
+        return time.perf_counter() - t0, res
+
+    def best(plan):
+        run(plan)
+        dts = [run(plan) for _ in range(max(2, args.steps // 3))]
+        return min(dts, key=lambda z: z[0])
+
+    irp = apcg.batch_ir_plan_create(ctx, B.sys_row_off, rowptr, col, None, val32,
+                                    apcg.ir_opts(rtol=1e-10, rtol_inner=1e-4, inner_check_every=4))
+    table_ir = apcg.batch_plan_tune(irp, b) if not args.no_tune else None
+    dt_ir, res_ir = best(irp)
+    x_ir = x.cpu().numpy()
+    assert all(r["reason"] == "converged" for r in res_ir)
+    apcg.call("apcg_batch_plan_destroy", V(irp))
+    inner = np.array([r["iters"] for r in res_ir])
+    outer = np.array([r["outer"] for r in res_ir])
+    out["batched_ir"] = {"ms_per_batch": 1e3 * dt_ir, "solves_per_s": B.nsys / dt_ir, "inner_total": int(inner.sum()),
+                         "outer_max": int(outer.max()), "outer_mean": float(outer.mean()),
+                         "max_rel_res": max(r["rel_res"] for r in res_ir), "tuning_table": table_ir}
+    cgp = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, val64, apcg.cg_opts(rtol=1e-10, check_every=4))
+    if not args.no_tune:
+        apcg.batch_plan_tune(cgp, b)
+    dt_64, res_64 = best(cgp)
+    x_64 = x.cpu().numpy()
+    assert all(r["reason"] == "converged" for r in res_64)
+    apcg.call("apcg_batch_plan_destroy", V(cgp))
+    it64 = np.array([r["iters"] for r in res_64])
+    out["batched_fp64"] = {"ms_per_batch": 1e3 * dt_64, "solves_per_s": B.nsys / dt_64, "iters_total": int(it64.sum())}
+    out["speedup_ir_vs_fp64_batched"] = dt_64 / dt_ir
+    # float64 one system at a time (the single-system solver's auto mode), on a sample scaled to the batch
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(B.nsys, 256, replace=False))
+    systems = []
+    for s in sample:
+        A_s, b_s, _ = B.system(int(s))
+        d = {"rowptr": t(A_s.rowptr), "col": t(A_s.col), "val": t(A_s.val), "b": t(b_s)}
+        d["x"] = torch.zeros(A_s.n, dtype=torch.float64, device=dev)
+        d["A"] = apcg.mat_wrap(d["rowptr"], d["col"], d["val"])
+        d["vb"], d["vx"] = apcg.vec_wrap(d["b"]), apcg.vec_wrap(d["x"])
+        d["plan"] = apcg.cg_plan_create(ctx, d["A"], apcg.cg_opts(rtol=1e-10, check_every=4, mode="auto"))
+        systems.append(d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d in systems:
+        r = apcg.cg_plan_solve(d["plan"], d["vb"], d["vx"])
+        assert r["reason"] == "converged"
+    dt_seq = (time.perf_counter() - t0) * B.nsys / len(sample)
+    for d in systems:
+        apcg.call("apcg_cg_plan_destroy", V(d["plan"]))
+        for h, fn in ((d["vb"], "apcg_vec_destroy"), (d["vx"], "apcg_vec_destroy"), (d["A"], "apcg_mat_destroy")):
+            apcg.call(fn, V(h))
+    out["one_at_a_time_fp64"] = {"ms_per_batch": 1e3 * dt_seq, "solves_per_s": B.nsys / dt_seq,
+                                 "sample": "256 random systems timed, scaled to 4096"}
+    out["speedup_ir_batched_vs_one_at_a_time"] = dt_seq / dt_ir
+    # error of the refinement against the batched float64 solution, over the whole batch
+    # (the comparison with the float64 oracle runs in the tests)
+    off = B.sys_row_off
+    err_64 = max(np.linalg.norm(x_ir[off[s]:off[s + 1]] - x_64[off[s]:off[s + 1]]) /
+                 max(np.linalg.norm(x_64[off[s]:off[s + 1]]), 1e-300) for s in range(B.nsys))
+    out["max_rel_err_vs_fp64_batched"] = float(err_64)
+    line = {"metric": "batched mixed-precision solves/s at rtol 1e-10", "value": B.nsys / dt_ir, "unit": "solves/s",
+            "dtype": "f32+f64", "data": "synthetic", **out}
     print(json.dumps(line), flush=True)
 
 

@@ -499,14 +499,32 @@ APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apc
 typedef struct apcg_batch_plan_s* apcg_batch_plan;
 
 typedef struct {
-  int32_t iters;   /* completed iterations of this system */
+  int32_t iters;   /* completed iterations of this system (refinement: inner iterations summed) */
   int32_t reason;  /* apcg_reason */
-  double rel_res;  /* ||r|| / ||b|| at the last convergence test (recursive residual) */
+  double rel_res;  /* ||r|| / ||b|| at the last convergence test (CG: recursive residual;
+                      refinement: the float64 true residual b - A x) */
+  int32_t outer;   /* refinement: corrections applied; 0 for CG */
+  int32_t pad;
 } apcg_batch_result;
 
 APCG_API apcg_status apcg_batch_plan_create(apcg_ctx ctx, int32_t nsys, const int32_t* sys_row_off,
                                             const int32_t* rowptr, const int32_t* col, const double* val,
                                             const apcg_cg_opts* opts, apcg_batch_plan* out);
+/*
+ * Batched mixed-precision refinement: every system is solved by the scheme of
+ * apcg_ir_plan_create (float64 true residual and update, float32 Jacobi-PCG
+ * for each correction started from zero, Sec. 3.3's CG in the inner loop), all
+ * of it inside the system's cluster in one launch.  val (float64) serves the
+ * outer residual and val32 (float32) the inner solves; either may be NULL:
+ * a NULL val widens val32 (exact when the float32 values are the matrix), a
+ * NULL val32 rounds val to nearest in the kernel.  The inner Jacobi diagonal
+ * is the float32 one.  opts NULL selects apcg_ir_opts_default.  The plan is
+ * solved, tuned and destroyed with the apcg_batch_plan_* calls below.
+ */
+APCG_API apcg_status apcg_batch_ir_plan_create(apcg_ctx ctx, int32_t nsys, const int32_t* sys_row_off,
+                                               const int32_t* rowptr, const int32_t* col, const double* val,
+                                               const float* val32, const apcg_ir_opts* opts,
+                                               apcg_batch_plan* out);
 /* Solve all systems; results (host [nsys]) may be NULL.  Blocks until done when results != NULL. */
 APCG_API apcg_status apcg_batch_plan_solve(apcg_batch_plan plan, const double* b, double* x,
                                            apcg_batch_result* results);

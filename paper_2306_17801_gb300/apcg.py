@@ -130,7 +130,13 @@ class IrResult(C.Structure):
 
 
 class BatchResult(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rel_res", C.c_double)]
+    _fields_ = [
+        ("iters", C.c_int32),
+        ("reason", C.c_int32),
+        ("rel_res", C.c_double),
+        ("outer", C.c_int32),
+        ("pad", C.c_int32),
+    ]
 
 
 REASONS[3] = "bad_diagonal"
@@ -210,6 +216,7 @@ PROTOS = {
     "apcg_ir_plan_destroy": [P],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
     "apcg_batch_plan_create": [P, i32, P, P, P, P, C.POINTER(CgOpts), PP],
+    "apcg_batch_ir_plan_create": [P, i32, P, P, P, P, P, C.POINTER(IrOpts), PP],
     "apcg_batch_plan_solve": [P, P, P, P],
     "apcg_batch_plan_tune": [P, P, C.c_char_p, C.c_size_t],
     "apcg_batch_plan_destroy": [P],
@@ -264,7 +271,9 @@ def _out():
 
 
 def _ptr(t) -> int:
-    """Raw data pointer of a tensor (or an int pointer)."""
+    """Raw data pointer of a tensor (or an int pointer; None is NULL)."""
+    if t is None:
+        return 0
     return t if isinstance(t, int) else int(t.data_ptr())
 
 
@@ -465,7 +474,23 @@ def batch_plan_solve(plan, b, x, nsys: int | None = None):
         return None
     res = (BatchResult * nsys)()
     call("apcg_batch_plan_solve", C.c_void_p(plan), C.c_void_p(_ptr(b)), C.c_void_p(_ptr(x)), res)
-    return [{"iters": int(r.iters), "reason": REASONS.get(int(r.reason), int(r.reason)), "rel_res": float(r.rel_res)} for r in res]
+    return [
+        {"iters": int(r.iters), "reason": REASONS.get(int(r.reason), int(r.reason)), "rel_res": float(r.rel_res), "outer": int(r.outer)}
+        for r in res
+    ]
+
+
+def batch_ir_plan_create(ctx, sys_row_off, rowptr, col, val, val32, opts: IrOpts):
+    """Batched mixed-precision refinement plan; val (float64) and val32 (float32) CUDA tensors, either may be None."""
+    import numpy as np
+
+    off = np.ascontiguousarray(sys_row_off, dtype=np.int32)
+    h = _out()
+    call(
+        "apcg_batch_ir_plan_create", C.c_void_p(ctx), off.shape[0] - 1, off.ctypes.data_as(P), C.c_void_p(_ptr(rowptr)),
+        C.c_void_p(_ptr(col)), C.c_void_p(_ptr(val)), C.c_void_p(_ptr(val32)), C.byref(opts), C.byref(h),
+    )
+    return h.value
 
 
 def batch_plan_tune(plan, b) -> list[tuple]:

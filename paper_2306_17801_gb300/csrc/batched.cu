@@ -51,7 +51,10 @@ struct apcg_batch_plan_s {
   const int32_t* rowptr = nullptr;
   const int32_t* col = nullptr;
   const double* val = nullptr;
+  const float* val32 = nullptr;  // refinement: float32 values (or nullptr: val rounded in the kernel)
+  bool ir = false;               // mixed-precision refinement per system
   apcg_cg_opts opts{};
+  apcg_ir_opts iropts{};
   std::vector<int32_t> n;
   std::vector<BatchClass> classes;
   char* ws = nullptr;
@@ -70,10 +73,10 @@ struct apcg_batch_plan_s {
 namespace apcg {
 namespace {
 
-ClusterShape shape_for_target(int n_hi, int target) {
+ClusterShape shape_for_target(int n_hi, int target, bool ir) {
   int C = 1;
   while (C < 16 && cluster_rows_per_cta(n_hi, C) > target) C *= 2;
-  return schedulable_shape(n_hi, C);
+  return schedulable_shape(n_hi, C, ir);
 }
 
 ClusterArgs class_args(apcg_batch_plan P, const BatchClass& c, const double* b, double* x) {
@@ -94,6 +97,15 @@ ClusterArgs class_args(apcg_batch_plan P, const BatchClass& c, const double* b, 
   a.atol = P->opts.atol;
   a.max_it = P->opts.max_it;
   a.hist_len = 0;
+  if (P->ir) {
+    a.val32 = P->val32;
+    a.rtol = P->iropts.rtol;
+    a.atol = P->iropts.atol;
+    a.max_it = P->iropts.max_inner;
+    a.check_every = P->iropts.inner_check_every;
+    a.rtol_inner = P->iropts.rtol_inner;
+    a.max_outer = P->iropts.max_outer;
+  }
   return a;
 }
 
@@ -169,9 +181,13 @@ using namespace apcg;
 
 extern "C" {
 
-apcg_status apcg_batch_plan_create(apcg_ctx ctx_in, int32_t nsys, const int32_t* sys_row_off, const int32_t* rowptr,
-                                   const int32_t* col, const double* val, const apcg_cg_opts* opts,
-                                   apcg_batch_plan* out) {
+}  // extern "C"
+
+namespace {
+
+apcg_status create_plan(apcg_ctx ctx_in, int32_t nsys, const int32_t* sys_row_off, const int32_t* rowptr,
+                        const int32_t* col, const double* val, const float* val32, const apcg_cg_opts* opts,
+                        const apcg_ir_opts* iropts, apcg_batch_plan* out) {
   APCG_CHECK(out && sys_row_off && rowptr, "NULL argument");
   APCG_CHECK(nsys >= 1, "nsys must be >= 1");
   APCG_CHECK(sys_row_off[0] == 0, "sys_row_off[0] must be 0");
@@ -187,6 +203,14 @@ apcg_status apcg_batch_plan_create(apcg_ctx ctx_in, int32_t nsys, const int32_t*
   else
     apcg_cg_opts_default(&o);
   APCG_CHECK(o.check_every >= 1 && o.rtol >= 0.0 && o.atol >= 0.0, "bad options");
+  if (iropts) {
+    APCG_CHECK(iropts->rtol >= 0.0 && iropts->atol >= 0.0 && iropts->max_outer >= 0 && iropts->max_inner >= 1 &&
+                   iropts->inner_check_every >= 1 && iropts->rtol_inner >= 0.0f && iropts->rtol_inner < 1.0f,
+               "bad refinement options");
+    APCG_CHECK(val || val32 || sys_row_off[nsys] == 0, "refinement needs float64 or float32 values");
+  } else {
+    APCG_CHECK(val || sys_row_off[nsys] == 0, "val is NULL");
+  }
   apcg_ctx ctx;
   APCG_TRY(resolve_ctx(ctx_in, &ctx));
   std::unique_ptr<apcg_batch_plan_s, void (*)(apcg_batch_plan)> P(new apcg_batch_plan_s(), destroy_plan);
@@ -196,6 +220,9 @@ apcg_status apcg_batch_plan_create(apcg_ctx ctx_in, int32_t nsys, const int32_t*
   P->rowptr = rowptr;
   P->col = col;
   P->val = val;
+  P->val32 = val32;
+  P->ir = iropts != nullptr;
+  if (iropts) P->iropts = *iropts;
   P->opts = o;
   P->n.resize(nsys);
   std::vector<SysDesc> desc(nsys);
@@ -243,7 +270,7 @@ apcg_status apcg_batch_plan_create(apcg_ctx ctx_in, int32_t nsys, const int32_t*
                               ctx->stream));
     APCG_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
     APCG_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
-    const ClusterShape sh = shape_for_target(c.n_hi, kDefaultRowsPerCta);
+    const ClusterShape sh = shape_for_target(c.n_hi, kDefaultRowsPerCta, P->ir);
     if (!sh.ok) return set_error(APCG_ERR_UNSUPPORTED, "no schedulable cluster shape for systems of %d rows", c.n_hi);
     set_shape(c, sh);
   }
@@ -257,6 +284,27 @@ apcg_status apcg_batch_plan_create(apcg_ctx ctx_in, int32_t nsys, const int32_t*
   }
   *out = P.release();
   return APCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+apcg_status apcg_batch_plan_create(apcg_ctx ctx, int32_t nsys, const int32_t* sys_row_off, const int32_t* rowptr,
+                                   const int32_t* col, const double* val, const apcg_cg_opts* opts,
+                                   apcg_batch_plan* out) {
+  return create_plan(ctx, nsys, sys_row_off, rowptr, col, val, nullptr, opts, nullptr, out);
+}
+
+apcg_status apcg_batch_ir_plan_create(apcg_ctx ctx, int32_t nsys, const int32_t* sys_row_off, const int32_t* rowptr,
+                                      const int32_t* col, const double* val, const float* val32,
+                                      const apcg_ir_opts* opts, apcg_batch_plan* out) {
+  apcg_ir_opts o;
+  if (opts)
+    o = *opts;
+  else
+    apcg_ir_opts_default(&o);
+  return create_plan(ctx, nsys, sys_row_off, rowptr, col, val, val32, nullptr, &o, out);
 }
 
 apcg_status apcg_batch_plan_solve(apcg_batch_plan P, const double* b, double* x, apcg_batch_result* results) {
@@ -293,6 +341,8 @@ apcg_status apcg_batch_plan_solve(apcg_batch_plan P, const double* b, double* x,
                                               : APCG_BREAKDOWN;
     const double bn = std::sqrt(r.bnorm2);
     o.rel_res = bn > 0.0 ? std::sqrt(r.rr) / bn : std::sqrt(r.rr);
+    o.outer = r.outer;
+    o.pad = 0;
   }
   return APCG_OK;
 }
@@ -315,7 +365,7 @@ apcg_status apcg_batch_plan_tune(apcg_batch_plan P, const double* b, char* table
     ClusterShape tried[8];
     int ntried = 0;
     for (int target : kTuneTargets) {
-      const ClusterShape sh = shape_for_target(c.n_hi, target);
+      const ClusterShape sh = shape_for_target(c.n_hi, target, P->ir);
       if (!sh.ok) continue;
       bool dup = false;
       for (int i = 0; i < ntried; ++i) dup |= tried[i].C == sh.C;

@@ -2,124 +2,99 @@
 //
 // For systems small enough that a kernel launch costs more than an
 // iteration's work, the entire solve runs in one launch: a cluster of C CTAs
-// (one per SM, C <= 16) owns one system.  CTA `rank` owns a contiguous slice
-// of rpc = 2^shift rows; each thread keeps x, r, z, D^-1 and w of its rows in
-// registers, and the CTA keeps its slice of p in shared memory, where the
-// other CTAs of the cluster read it through distributed shared memory during
-// the SpMV.  The two reductions of an iteration ((p,w); (r,z) with (r,r) on
-// test iterations) are block sums published to a shared-memory slot and
-// combined after a cluster barrier by every CTA in the same fixed rank order,
-// so every CTA holds bit-identical alpha, beta and convergence decisions and
-// the control flow stays uniform across the cluster.  A third cluster barrier
-// per iteration publishes the updated p.  No host round trip, no grid-wide
-// synchronisation and no global-memory reduction are needed.
-//
-// The arithmetic is the textbook Jacobi-PCG of Sec. 4.1-4.2 in the step order
-// of the mixed-API CG example of Sec. 3.3, as in cg.cu.  Batched solves run a
-// persistent grid of clusters that take systems from an atomic work queue in
-// longest-first order.
+// (one per SM, C <= 16) owns one system (geometry and iteration loop in
+// cluster_loop.cuh).  Two kernels:
+//   cg_cluster_kernel     float64 Jacobi-PCG (the paper's method, Sec. 4.2, in
+//                         the step order of the mixed-API example of Sec. 3.3);
+//   cg_cluster_ir_kernel  float64 iterative refinement around a float32
+//                         Jacobi-PCG (the mixed-precision extension): the
+//                         outer residual r = b - A x, its norm and x += d in
+//                         float64, the inner solve entirely in float32.
+// No host round trip, no grid-wide synchronisation and no global-memory
+// reduction are needed.  Batched solves run a persistent grid of clusters that
+// take systems from an atomic work queue in longest-first order.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
-#include <cstring>
-#include <memory>
-#include <numeric>
-#include <vector>
 
 #include "apcg_internal.hpp"
 #include "cg_internal.hpp"
 #include "cluster_cg.hpp"
-#include "kernels_common.cuh"
-
-namespace cgx = cooperative_groups;
+#include "cluster_loop.cuh"
 
 namespace apcg {
 namespace {
 
-constexpr int kMaxCluster = 16;
+using clu::cgx::cluster_group;
 
-// Sum NV values over the cluster.  Every thread of every CTA returns the same
-// totals (ranks combined in order 0..C-1 by the same warp tree everywhere).
-template <int NV>
-__device__ __forceinline__ void cluster_sum(double (&v)[NV], double* s_red, double (*s_slot)[4],
-                                            double* const* s_peer_slot, double* s_tot, int& parity, int C,
-                                            cgx::cluster_group& cl) {
-  dev::block_sum<NV>(v, s_red);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) s_slot[parity][k] = v[k];
-  }
-  cl.sync();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = lane < C ? s_peer_slot[lane][parity * 4 + k] : 0.0;
-      t = dev::warp_sum(t);
-      if (lane == 0) s_tot[k] = t;
-    }
+// Shared-memory bookkeeping common to both kernels; returns the Shared view.
+struct Block {
+  double slot[2][4];
+  double red[4 * kClusterThreads];
+  double tot[4];
+  double* peer_slot[clu::kMaxCluster];
+  void* peer_data[2][clu::kMaxCluster];  // the dynamic arrays of every CTA
+  int sys;
+};
+
+__device__ clu::Shared setup_block(Block& B, cluster_group& cl, void* dyn0, void* dyn1) {
+  const int C = (int)cl.num_blocks();
+  if (threadIdx.x < C) {
+    B.peer_slot[threadIdx.x] = cl.map_shared_rank(&B.slot[0][0], (unsigned)threadIdx.x);
+    B.peer_data[0][threadIdx.x] = cl.map_shared_rank(dyn0, (unsigned)threadIdx.x);
+    B.peer_data[1][threadIdx.x] = dyn1 ? cl.map_shared_rank(dyn1, (unsigned)threadIdx.x) : nullptr;
   }
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = s_tot[k];
-  parity ^= 1;
+  clu::Shared S;
+  S.slot = &B.slot[0][0];
+  S.peer_slot = B.peer_slot;
+  S.red = B.red;
+  S.tot = B.tot;
+  S.C = C;
+  S.rank = (int)cl.block_rank();
+  return S;
+}
+
+// Next system index of the cluster's work queue (uniform across the cluster).
+__device__ int next_system(Block& B, const ClusterArgs& a, cluster_group& cl, int rank) {
+  if (rank == 0 && threadIdx.x == 0) B.sys = (int)atomicAdd(a.next, 1u);
+  cl.sync();
+  const int idx = *cl.map_shared_rank(&B.sys, 0u);
+  cl.sync();  // every CTA has read the index before rank 0 may overwrite it or exit
+  return idx;
 }
 
 template <int R>
 __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(ClusterArgs a) {
-  cgx::cluster_group cl = cgx::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const int tpb = blockDim.x;
+  cluster_group cl = clu::cgx::this_cluster();
   extern __shared__ double s_p[];  // this CTA's slice of p
-  __shared__ double s_slot[2][4];
-  __shared__ double s_red[4 * kClusterThreads];
-  __shared__ double s_tot[4];
-  __shared__ double* s_peer[kMaxCluster];
-  __shared__ double* s_peer_slot[kMaxCluster];
-  __shared__ int s_sys;
-  if (threadIdx.x < C) {
-    s_peer[threadIdx.x] = cl.map_shared_rank(s_p, (unsigned)threadIdx.x);
-    s_peer_slot[threadIdx.x] = cl.map_shared_rank(&s_slot[0][0], (unsigned)threadIdx.x);
-  }
-  __syncthreads();
+  __shared__ Block B;
+  const clu::Shared S = setup_block(B, cl, s_p, nullptr);
+  double* const* peer_p = reinterpret_cast<double* const*>(B.peer_data[0]);
   int parity = 0;
   for (;;) {
-    if (rank == 0 && threadIdx.x == 0) s_sys = (int)atomicAdd(a.next, 1u);
-    cl.sync();
-    const int idx = *cl.map_shared_rank(&s_sys, 0u);
-    cl.sync();  // every CTA has read the index before rank 0 may overwrite it or exit
+    const int idx = next_system(B, a, cl, S.rank);
     if (idx >= a.nsys) break;
     const int s = a.order ? a.order[idx] : idx;
     const SysDesc d = a.sys[s];
-    const int n = d.n;
     const int64_t row0 = d.row0;
-    int shift = 0;
-    while (((n + C - 1) / C) > (1 << shift)) ++shift;
-    const int rpc = 1 << shift;
-    const int lbase = rank * rpc;
-    const int32_t* __restrict__ rowptr = a.rowptr + row0;
-    const int32_t* __restrict__ col = a.col;
-    const double* __restrict__ val = a.val;
-    double xk[R], rk[R], zk[R], dk[R], wk[R];
-    int lk[R];
-    bool vk[R];
+    const clu::Rows g = clu::make_rows(d.n, S.C, S.rank, a.rowptr + row0, a.col);
+    double xk[R], rk[R], zk[R], dk[R];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      const int loc = threadIdx.x + k * tpb;
-      lk[k] = loc;
-      vk[k] = loc < rpc && lbase + loc < n;
-      xk[k] = rk[k] = zk[k] = dk[k] = wk[k] = 0.0;
-      if (vk[k]) {
-        const int i = lbase + loc;
-        const int32_t e0 = rowptr[i], e1 = rowptr[i + 1];
+      xk[k] = rk[k] = zk[k] = dk[k] = 0.0;
+      if (clu::owns<R>(g, k)) {
+        const int loc = threadIdx.x + k * blockDim.x;
+        const int i = g.lbase + loc;
+        const int32_t e0 = g.rowptr[i], e1 = g.rowptr[i + 1];
         double ax = 0.0, dg = 0.0;
         for (int32_t e = e0; e < e1; ++e) {
-          const int32_t j = col[e];
-          const double aij = val[e];
+          const int32_t j = g.col[e];
+          const double aij = a.val[e];
           ax = fma(aij, a.x[row0 + j], ax);
           if (j == i) dg += aij;
         }
@@ -142,137 +117,239 @@ __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(ClusterArgs
         v[2] = fma(bi, bi, v[2]);
       }
     }
-    cluster_sum<4>(v, s_red, s_slot, s_peer_slot, s_tot, parity, C, cl);
-    double rho = v[0], rr = v[1];
+    clu::cluster_sum<4>(v, S, parity, cl);  // also publishes p = z
+    double rr = v[1];
     const double bb = v[2];
     const double tol = fmax(a.rtol * sqrt(bb), a.atol);
-    const int max_it = a.max_it > 0 ? a.max_it : (n > 0 ? 10 * n : 10);
-    const int kchk = a.check_every;
-    const bool record = (a.hist_len > 0) && (idx == 0) && rank == 0 && threadIdx.x == 0;
-    int it = 0;
-    int done = 0;
+    const int max_it = a.max_it > 0 ? a.max_it : (d.n > 0 ? 10 * d.n : 10);
+    int it = 0, done = 0;
     if (v[3] > 0.0)
       done = kDoneBadDiagonal;
     else if (sqrt(rr) <= tol)
       done = kDoneConverged;
-    while (!done) {
-      // w = A p (p of other CTAs through distributed shared memory)
-      double g[1] = {0.0};
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        if (vk[k]) {
-          const int i = lbase + lk[k];
-          const int32_t e0 = rowptr[i], e1 = rowptr[i + 1];
-          double w = 0.0;
-          for (int32_t e = e0; e < e1; ++e) {
-            const int32_t j = col[e];
-            const int owner = j >> shift;
-            const int lj = j & (rpc - 1);
-            const double pj = owner == rank ? s_p[lj] : s_peer[owner][lj];
-            w = fma(val[e], pj, w);
-          }
-          wk[k] = w;
-          g[0] = fma(s_p[lk[k]], w, g[0]);
-        }
-      }
-      cluster_sum<1>(g, s_red, s_slot, s_peer_slot, s_tot, parity, C, cl);
-      const double gamma = g[0];
-      if (!(gamma > 0.0) || !isfinite(gamma)) {
-        done = kDoneBreakdown;
-        break;
-      }
-      const double alpha = rho / gamma;
-      if (record && it < a.hist_len) a.alpha_h[it] = alpha;
-      ++it;
-      const bool check = (it % kchk == 0) || it >= max_it;
-      double u[2] = {0.0, 0.0};
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        if (vk[k]) {
-          xk[k] = fma(alpha, s_p[lk[k]], xk[k]);
-          rk[k] = fma(-alpha, wk[k], rk[k]);
-          zk[k] = dk[k] * rk[k];
-          u[0] = fma(rk[k], zk[k], u[0]);
-          if (check) u[1] = fma(rk[k], rk[k], u[1]);
-        }
-      }
-      cluster_sum<2>(u, s_red, s_slot, s_peer_slot, s_tot, parity, C, cl);
-      const double rz = u[0];
-      if (check) rr = u[1];
-      if ((check && rr == 0.0) || rz == 0.0)
-        done = kDoneConverged;
-      else if (check && sqrt(rr) <= tol)
-        done = kDoneConverged;
-      else if (it >= max_it)
-        done = kDoneNotConverged;
-      else if (!isfinite(rz) || (check && !isfinite(rr)))
-        done = kDoneBreakdown;
-      if (done) break;
-      const double beta = rz / rho;
-      rho = rz;
-      if (record && it - 1 < a.hist_len) a.beta_h[it - 1] = beta;
-#pragma unroll
-      for (int k = 0; k < R; ++k)
-        if (vk[k]) s_p[lk[k]] = fma(beta, s_p[lk[k]], zk[k]);
-      cl.sync();  // the new p is visible to the whole cluster before the next SpMV
-    }
+    else
+      done = clu::pcg_loop<R, double, double>(g, a.val, s_p, peer_p, xk, rk, zk, dk, v[0], rr, tol, max_it,
+                                              a.check_every, S, parity, cl, a.alpha_h, a.beta_h,
+                                              idx == 0 ? a.hist_len : 0, &it);
 #pragma unroll
     for (int k = 0; k < R; ++k)
-      if (vk[k]) a.x[row0 + lbase + lk[k]] = xk[k];
-    if (rank == 0 && threadIdx.x == 0) {
+      if (clu::owns<R>(g, k)) a.x[row0 + g.lbase + threadIdx.x + k * blockDim.x] = xk[k];
+    if (S.rank == 0 && threadIdx.x == 0) {
       SysResult* res = a.res + s;
       res->iters = it;
       res->done = done;
       res->rr = rr;
       res->bnorm2 = bb;
+      res->outer = 0;
     }
   }
 }
 
-template <int R>
-cudaError_t launch_r(const ClusterArgs& args, const ClusterShape& sh, int nclusters, cudaStream_t s) {
-  auto kern = cg_cluster_kernel<R>;
-  const size_t smem = sizeof(double) * (size_t)sh.rpc_max;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) return e;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+// Matrix value as float64 (outer residual) or float32 (inner solve).
+__device__ __forceinline__ double val64(const ClusterArgs& a, int64_t e) {
+  return a.val ? a.val[e] : (double)a.val32[e];
+}
+__device__ __forceinline__ float val32(const ClusterArgs& a, int64_t e) {
+  return a.val32 ? a.val32[e] : (float)a.val[e];
+}
+
+// Float64 refinement around a float32 Jacobi-PCG, one cluster per system.
+// Shared memory: the CTA's slice of x (float64, read by the other CTAs in the
+// outer residual) followed by its slice of the inner p (float32).
+// TI: the type of the values the inner solve reads (float: val32; double: val rounded as read).
+template <int R, class TI>
+__global__ void __launch_bounds__(kClusterThreads, (R >= 8 ? 1 : 2)) cg_cluster_ir_kernel(ClusterArgs a, int rpc_max) {
+  const TI* const vin = std::is_same<TI, float>::value ? (const TI*)a.val32 : (const TI*)a.val;
+  cluster_group cl = clu::cgx::this_cluster();
+  extern __shared__ double s_dyn[];
+  double* s_x = s_dyn;
+  float* s_p = reinterpret_cast<float*>(s_dyn + rpc_max);
+  __shared__ Block B;
+  const clu::Shared S = setup_block(B, cl, s_x, s_p);
+  double* const* peer_x = reinterpret_cast<double* const*>(B.peer_data[0]);
+  float* const* peer_p = reinterpret_cast<float* const*>(B.peer_data[1]);
+  int parity = 0;
+  for (;;) {
+    const int idx = next_system(B, a, cl, S.rank);
+    if (idx >= a.nsys) break;
+    const int s = a.order ? a.order[idx] : idx;
+    const SysDesc d = a.sys[s];
+    const int64_t row0 = d.row0;
+    const clu::Rows g = clu::make_rows(d.n, S.C, S.rank, a.rowptr + row0, a.col);
+    // Float32 Jacobi diagonal and the float64 start.
+    double xk[R];
+    float dk[R];
+    float bad[1] = {0.0f};
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      xk[k] = 0.0;
+      dk[k] = 0.0f;
+      if (clu::owns<R>(g, k)) {
+        const int loc = threadIdx.x + k * blockDim.x;
+        const int i = g.lbase + loc;
+        float dg = 0.0f;
+        for (int32_t e = g.rowptr[i]; e < g.rowptr[i + 1]; ++e)
+          if (g.col[e] == i) dg += val32(a, e);
+        const bool b_ = !(dg != 0.0f) || !isfinite(dg);
+        dk[k] = b_ ? 0.0f : 1.0f / dg;
+        if (b_) bad[0] += 1.0f;
+        xk[k] = a.x[row0 + i];
+      }
+    }
+    clu::cluster_sum<1>(bad, S, parity, cl);
+    int done = bad[0] > 0.0f ? kDoneBadDiagonal : 0;
+    int outer = 0, inner_total = 0;
+    double rr64 = 0.0, bb = 0.0;
+    while (!done) {
+      // r = b - A x in float64 (x of other CTAs through distributed shared memory)
+#pragma unroll
+      for (int k = 0; k < R; ++k)
+        if (clu::owns<R>(g, k)) s_x[threadIdx.x + k * blockDim.x] = xk[k];
+      cl.sync();
+      double r64[R];
+      double v[2] = {0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        r64[k] = 0.0;
+        if (clu::owns<R>(g, k)) {
+          const int i = g.lbase + threadIdx.x + k * blockDim.x;
+          double ax = 0.0;
+          for (int32_t e = g.rowptr[i]; e < g.rowptr[i + 1]; ++e) {
+            const int32_t j = g.col[e];
+            const int owner = j >> g.shift;
+            const int lj = j & (g.rpc - 1);
+            const double xj = owner == S.rank ? s_x[lj] : peer_x[owner][lj];
+            ax = fma(val64(a, e), xj, ax);
+          }
+          const double bi = a.b[row0 + i];
+          r64[k] = bi - ax;
+          v[0] = fma(r64[k], r64[k], v[0]);
+          v[1] = fma(bi, bi, v[1]);
+        }
+      }
+      clu::cluster_sum<2>(v, S, parity, cl);
+      rr64 = v[0];
+      bb = v[1];
+      if (!isfinite(rr64)) {
+        done = kDoneBreakdown;
+        break;
+      }
+      if (sqrt(rr64) <= fmax(a.rtol * sqrt(bb), a.atol)) {
+        done = kDoneConverged;
+        break;
+      }
+      if (outer == a.max_outer) {
+        done = kDoneNotConverged;
+        break;
+      }
+      // Inner float32 solve of A d = (float) r from d = 0.
+      float dd[R], rk[R], zk[R];
+      float u[2] = {0.0f, 0.0f};
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        dd[k] = rk[k] = zk[k] = 0.0f;
+        if (clu::owns<R>(g, k)) {
+          rk[k] = (float)r64[k];
+          zk[k] = dk[k] * rk[k];
+          s_p[threadIdx.x + k * blockDim.x] = zk[k];
+          u[0] = fmaf(rk[k], zk[k], u[0]);
+          u[1] = fmaf(rk[k], rk[k], u[1]);
+        }
+      }
+      clu::cluster_sum<2>(u, S, parity, cl);  // also publishes p = z
+      float rr32 = u[1];
+      const float tol32 = a.rtol_inner * sqrtf(rr32);
+      if (!(rr32 > 0.0f)) {  // the float32 right-hand side vanished: no further progress possible
+        done = kDoneNotConverged;
+        break;
+      }
+      int it = 0;
+      const int inner_done = clu::pcg_loop<R, float, TI>(g, vin, s_p, peer_p, dd, rk, zk, dk, u[0], rr32, tol32,
+                                                         a.max_it, a.check_every, S, parity, cl, nullptr, nullptr, 0,
+                                                         &it);
+      (void)inner_done;  // a breakdown or the cap still leaves a usable correction
+      inner_total += it;
+#pragma unroll
+      for (int k = 0; k < R; ++k) xk[k] += (double)dd[k];
+      ++outer;
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (clu::owns<R>(g, k)) a.x[row0 + g.lbase + threadIdx.x + k * blockDim.x] = xk[k];
+    if (S.rank == 0 && threadIdx.x == 0) {
+      SysResult* res = a.res + s;
+      res->iters = inner_total;
+      res->done = done;
+      res->rr = rr64;
+      res->bnorm2 = bb;
+      res->outer = outer;
+    }
   }
+}
+
+size_t smem_bytes(const ClusterShape& sh) {
+  return (size_t)sh.rpc_max * (sh.ir ? sizeof(double) + sizeof(float) : sizeof(double));
+}
+
+template <class K>
+cudaError_t prepare(K kern, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+cudaLaunchConfig_t make_cfg(const ClusterShape& sh, int nclusters, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nclusters * sh.C), 1, 1);
   cfg.blockDim = dim3((unsigned)sh.tpb, 1, 1);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = smem_bytes(sh);
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)sh.C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args);
+  return cfg;
+}
+
+template <int R>
+cudaError_t launch_r(const ClusterArgs& args, const ClusterShape& sh, int nclusters, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = make_cfg(sh, nclusters, s, attr);
+  if (sh.ir) {
+    auto kern = args.val32 ? cg_cluster_ir_kernel<R, float> : cg_cluster_ir_kernel<R, double>;
+    cudaError_t e = prepare(kern, cfg.dynamicSmemBytes);
+    return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, kern, args, sh.rpc_max);
+  }
+  auto kern = cg_cluster_kernel<R>;
+  cudaError_t e = prepare(kern, cfg.dynamicSmemBytes);
+  return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, kern, args);
 }
 
 template <int R>
 int max_clusters_r(const ClusterShape& sh) {
-  auto kern = cg_cluster_kernel<R>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  const size_t smem = sizeof(double) * (size_t)sh.rpc_max;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)sh.C, 1, 1);
-  cfg.blockDim = dim3((unsigned)sh.tpb, 1, 1);
-  cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)sh.C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  const cudaLaunchConfig_t cfg = make_cfg(sh, 1, nullptr, attr);
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+  cudaError_t e;
+  if (sh.ir) {
+    // both value types have the same footprint class; take the larger
+    int n2 = 0;
+    auto k1 = cg_cluster_ir_kernel<R, float>;
+    auto k2 = cg_cluster_ir_kernel<R, double>;
+    e = prepare(k1, cfg.dynamicSmemBytes);
+    if (e == cudaSuccess) e = prepare(k2, cfg.dynamicSmemBytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k1, &cfg);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n2, k2, &cfg);
+    if (e == cudaSuccess) n = std::min(n, n2);
+  } else {
+    auto kern = cg_cluster_kernel<R>;
+    e = prepare(kern, cfg.dynamicSmemBytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+  }
+  if (e != cudaSuccess) {
     cudaGetLastError();
     n = 0;
   }
@@ -287,9 +364,10 @@ int cluster_rows_per_cta(int n, int C) {
   return 1 << shift;
 }
 
-ClusterShape cluster_shape_for(int n_max, int C) {
+ClusterShape cluster_shape_for(int n_max, int C, bool ir) {
   ClusterShape sh;
   sh.C = C;
+  sh.ir = ir;
   const int rpc = cluster_rows_per_cta(n_max, C);
   sh.rpc_max = rpc;
   sh.tpb = rpc >= kClusterThreads ? kClusterThreads : std::max(128, ((rpc + 31) / 32) * 32);
@@ -299,20 +377,19 @@ ClusterShape cluster_shape_for(int n_max, int C) {
   return sh;
 }
 
-ClusterShape schedulable_shape(int n_max, int C) {
-  // Halve the cluster until the device can hold one; larger slices per CTA follow.
-  ClusterShape sh = cluster_shape_for(n_max, C);
-  while (sh.ok && sh.C > 1 && max_active_clusters(sh) < 1) sh = cluster_shape_for(n_max, sh.C / 2);
+ClusterShape schedulable_shape(int n_max, int C, bool ir) {
+  ClusterShape sh = cluster_shape_for(n_max, C, ir);
+  while (sh.ok && sh.C > 1 && max_active_clusters(sh) < 1) sh = cluster_shape_for(n_max, sh.C / 2, ir);
   if (sh.ok && max_active_clusters(sh) < 1) sh.ok = false;
   return sh;
 }
 
-ClusterShape default_cluster_shape(int n) {
+ClusterShape default_cluster_shape(int n, bool ir) {
   // Spread small systems over as many SMs as a cluster has (the float64 pipe
   // of one SM retires two lanes per cycle), keeping at least 256 rows per CTA.
   int C = 1;
-  while (C < kMaxCluster && cluster_rows_per_cta(n, C) > 256) C *= 2;
-  return schedulable_shape(n, C);
+  while (C < clu::kMaxCluster && cluster_rows_per_cta(n, C) > 256) C *= 2;
+  return schedulable_shape(n, C, ir);
 }
 
 cudaError_t launch_cluster_cg(const ClusterArgs& args, const ClusterShape& sh, int nclusters, cudaStream_t s) {

@@ -1,0 +1,180 @@
+// Device building blocks of the whole-solve cluster kernels (cluster_cg.cu):
+// cluster-wide sums with bit-identical results in every CTA, and the
+// Jacobi-PCG iteration loop on the rows a cluster owns, for float64 solves and
+// for the float32 inner solves of mixed-precision refinement.
+//
+// A cluster of C CTAs owns one system.  CTA `rank` owns the slice of rows
+// [rank * rpc, (rank + 1) * rpc) (rpc = 2^shift); thread t owns the rows
+// rank * rpc + t + k * blockDim.x, k < R, and keeps their vector entries in
+// registers.  The CTA's slice of the search direction p lives in shared
+// memory, where the SpMV of every CTA reads it through distributed shared
+// memory.  All control decisions are taken from cluster sums that every CTA
+// forms in the same order, so the control flow is uniform across the cluster
+// and every cluster barrier is reached by all of its threads.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cg_internal.hpp"
+#include "kernels_common.cuh"
+
+namespace apcg {
+namespace clu {
+
+namespace cgx = cooperative_groups;
+
+constexpr int kMaxCluster = 16;
+
+// Shared-memory bookkeeping of the cluster sums.
+struct Shared {
+  double* slot;               // this CTA's published partial sums, [2][4]
+  double* const* peer_slot;   // the slot arrays of every CTA of the cluster, [C]
+  void* red;                  // block-sum scratch, 4 * blockDim.x values
+  double* tot;                // broadcast of the totals, [4]
+  int C, rank;
+};
+
+// Sum NV values over the cluster.  The CTA's block sums go to its slot, a
+// cluster barrier publishes them, and every CTA adds the C slots in rank
+// order with the same warp tree, so all threads of all CTAs get the same bits.
+// Slots alternate between two buffers: a buffer is rewritten only two sums
+// later, after a barrier that every CTA passes only once done reading it.
+template <int NV, class T>
+__device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& parity, cgx::cluster_group& cl) {
+  dev::block_sum<NV>(v, reinterpret_cast<T*>(S.red));
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) S.slot[parity * 4 + k] = (double)v[k];
+  }
+  cl.sync();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      T t = lane < S.C ? (T)S.peer_slot[lane][parity * 4 + k] : T(0);
+      t = dev::warp_sum(t);
+      if (lane == 0) S.tot[k] = (double)t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = (T)S.tot[k];
+  parity ^= 1;
+}
+
+// Geometry of the CTA's rows in the current system.
+struct Rows {
+  int shift, rpc, lbase, n;
+  const int32_t* rowptr;  // the system's rows (global nnz positions)
+  const int32_t* col;     // system-local column indices
+};
+
+__device__ __forceinline__ Rows make_rows(int n, int C, int rank, const int32_t* rowptr_sys, const int32_t* col) {
+  Rows g;
+  g.shift = 0;
+  while (((n + C - 1) / C) > (1 << g.shift)) ++g.shift;
+  g.rpc = 1 << g.shift;
+  g.lbase = rank * g.rpc;
+  g.n = n;
+  g.rowptr = rowptr_sys;
+  g.col = col;
+  return g;
+}
+
+template <int R>
+__device__ __forceinline__ bool owns(const Rows& g, int k) {
+  const int loc = threadIdx.x + k * blockDim.x;
+  return loc < g.rpc && g.lbase + loc < g.n;
+}
+
+// Jacobi-PCG iterations on the cluster's system until a test stops them.
+// On entry: rk = r, zk = D^-1 r, the CTA's slice s_p = z (published by a
+// cluster barrier), rho = (r, z); xk is the iterate, updated in place.  The
+// test runs when the iteration count is a multiple of kchk or reaches max_it.
+// Returns a kDone* code; *iters receives the completed iterations and rr the
+// (r,r) of the last test.  Values TV are widened to T.
+template <int R, class T, class TV>
+__device__ __forceinline__ int pcg_loop(const Rows& g, const TV* __restrict__ val, T* s_p, T* const* s_peer_p, T (&xk)[R],
+                        T (&rk)[R], T (&zk)[R], const T (&dk)[R], T rho, T& rr, T tol, int max_it, int kchk,
+                        const Shared& S, int& parity, cgx::cluster_group& cl, double* alpha_h, double* beta_h,
+                        int hist_len, int* iters) {
+  T wk[R];
+  int it = 0;
+  int done = 0;
+  while (!done) {
+    // w = A p (p of other CTAs through distributed shared memory)
+    T gsum[1] = {T(0)};
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      wk[k] = T(0);
+      if (owns<R>(g, k)) {
+        const int loc = threadIdx.x + k * blockDim.x;
+        const int i = g.lbase + loc;
+        const int32_t e0 = g.rowptr[i], e1 = g.rowptr[i + 1];
+        T w = T(0);
+        for (int32_t e = e0; e < e1; ++e) {
+          const int32_t j = g.col[e];
+          const int owner = j >> g.shift;
+          const int lj = j & (g.rpc - 1);
+          const T pj = owner == S.rank ? s_p[lj] : s_peer_p[owner][lj];
+          w = fma((T)val[e], pj, w);
+        }
+        wk[k] = w;
+        gsum[0] = fma(s_p[loc], w, gsum[0]);
+      }
+    }
+    cluster_sum<1>(gsum, S, parity, cl);
+    const T gamma = gsum[0];
+    if (!(gamma > T(0)) || !isfinite(gamma)) {
+      done = kDoneBreakdown;
+      break;
+    }
+    const T alpha = rho / gamma;
+    if (hist_len > 0 && it < hist_len && S.rank == 0 && threadIdx.x == 0) alpha_h[it] = alpha;
+    ++it;
+    const bool check = (it % kchk == 0) || it >= max_it;
+    T u[2] = {T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (owns<R>(g, k)) {
+        const int loc = threadIdx.x + k * blockDim.x;
+        xk[k] = fma(alpha, s_p[loc], xk[k]);
+        rk[k] = fma(-alpha, wk[k], rk[k]);
+        zk[k] = dk[k] * rk[k];
+        u[0] = fma(rk[k], zk[k], u[0]);
+        if (check) u[1] = fma(rk[k], rk[k], u[1]);
+      }
+    }
+    cluster_sum<2>(u, S, parity, cl);
+    const T rz = u[0];
+    if (check) rr = u[1];
+    if ((check && rr == T(0)) || rz == T(0))
+      done = kDoneConverged;
+    else if (check && sqrt(rr) <= tol)
+      done = kDoneConverged;
+    else if (it >= max_it)
+      done = kDoneNotConverged;
+    else if (!isfinite(rz) || (check && !isfinite(rr)))
+      done = kDoneBreakdown;
+    if (done) break;
+    const T beta = rz / rho;
+    rho = rz;
+    if (hist_len > 0 && it - 1 < hist_len && S.rank == 0 && threadIdx.x == 0) beta_h[it - 1] = beta;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (owns<R>(g, k)) {
+        const int loc = threadIdx.x + k * blockDim.x;
+        s_p[loc] = fma(beta, s_p[loc], zk[k]);
+      }
+    }
+    cl.sync();  // the new p is visible to the whole cluster before the next SpMV
+  }
+  *iters = it;
+  return done;
+}
+
+}  // namespace clu
+}  // namespace apcg
