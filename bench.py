@@ -112,7 +112,7 @@ def _traffic_record():
 
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
-        if rec.get("source_hash") != _build.source_hash():
+        if rec.get("unit_hash") != _build.unit_hash(rec.get("unit", "cg_core.cu")):
             return None
         return rec
     except Exception:

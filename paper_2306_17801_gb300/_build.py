@@ -51,6 +51,35 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def unit_hash(unit: str) -> str:
+    """sha256 over one translation unit and every local header it includes, transitively
+    (identifies the build of the kernels defined in that unit)."""
+    import hashlib
+    import re
+
+    inc = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+    dirs = [SRC_DIR, os.path.join(ROOT, "include")]
+    seen: dict[str, bytes] = {}
+    todo = [os.path.join(SRC_DIR, unit)]
+    while todo:
+        p = todo.pop()
+        if p in seen:
+            continue
+        with open(p, "rb") as f:
+            seen[p] = f.read()
+        for name in inc.findall(seen[p].decode("utf-8", "replace")):
+            for d in [os.path.dirname(p)] + dirs:
+                q = os.path.join(d, name)
+                if os.path.exists(q):
+                    todo.append(q)
+                    break
+    h = hashlib.sha256()
+    for p in sorted(seen):
+        h.update(os.path.basename(p).encode())
+        h.update(seen[p])
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
