@@ -47,11 +47,13 @@ apcg_status sell_layout(cudaStream_t s, int32_t n, const int32_t* rowptr_dev, Se
   counters().d2h_copies++;
   counters().d2h_bytes += (int64_t)(sizeof(int32_t) * rp.size());
   out->sptr.assign((size_t)out->nslices + 1, 0);
+  out->max_width = 0;
   int64_t acc = 0;
   for (int32_t sl = 0; sl < out->nslices; ++sl) {
     int32_t w = 0;
     const int32_t r1 = std::min(n, (sl + 1) * 32);
     for (int32_t r = sl * 32; r < r1; ++r) w = std::max(w, rp[r + 1] - rp[r]);
+    out->max_width = std::max(out->max_width, w);
     out->sptr[sl] = (int32_t)acc;
     acc += 32 * (int64_t)w;
     if (acc > (int64_t)INT32_MAX - 64)

@@ -65,7 +65,8 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
       // Long rows: groups of G entries per lane -- all column/value loads of a
       // group, then its gathers, then its FMAs; the last group is predicated
       // (the width is the same for the 32 lanes of a slice, so the predicate
-      // is uniform).
+      // is uniform).  Measured faster than whole groups plus single entries
+      // for the rest (27-point: 256 vs 285 us per launch at 160^3).
       for (int32_t k = 0; k < width; k += G) {
         int32_t j[G];
         TV a[G];

@@ -15,6 +15,7 @@ struct SellLayout {
   int32_t nslices = 0;
   int64_t padded = 0;          // entries including padding (multiple of 32)
   int32_t long_rows = 0;       // mean slice width >= 8
+  int32_t max_width = 0;       // entries per row of the widest slice
   std::vector<int32_t> sptr;   // [nslices + 1]
 };
 

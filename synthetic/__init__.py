@@ -20,6 +20,7 @@ from .stencils import (  # noqa: F401
     aniso_3d_7pt_fp32exact,
     diagonal_csr,
     random_spd_csr,
+    graph_laplacian_csr,
     sine_mode_2d,
     sine_mode_3d,
     rhs_from_solution,

@@ -206,6 +206,37 @@ def random_spd_csr(n: int, density: float, rng: np.random.Generator, dominance: 
     return CSR(m.indptr.astype(np.int32), m.indices.astype(np.int32), m.data.astype(np.float64))
 
 
+def graph_laplacian_csr(n: int, rng: np.random.Generator, mean_degree: float = 6.0, hub_degrees=(),
+                        shift: float = 1.0) -> CSR:
+    """Weighted graph Laplacian of a random graph plus shift * I (symmetric positive definite).
+
+    Rows of very different lengths: about n * mean_degree / 2 random edges
+    among the ordinary nodes (degrees roughly Poisson, some nodes isolated, so
+    their row holds only the diagonal), and hub nodes at evenly spaced indices,
+    hub h joined to exactly hub_degrees[h] distinct ordinary nodes (its row has
+    hub_degrees[h] + 1 entries).  Edge weights ~ U[0.5, 2].
+    """
+    hubs = np.array([(k + 1) * n // (len(hub_degrees) + 1) for k in range(len(hub_degrees))], dtype=np.int64)
+    ordinary = np.setdiff1d(np.arange(n, dtype=np.int64), hubs)
+    m = int(n * mean_degree / 2)
+    i = ordinary[rng.integers(0, ordinary.size, m)]
+    j = ordinary[rng.integers(0, ordinary.size, m)]
+    keep = i != j
+    i, j = i[keep], j[keep]
+    for h, d in zip(hubs, hub_degrees):
+        nb = rng.choice(ordinary, size=int(d), replace=False)
+        i = np.concatenate([i, np.full(nb.size, h)])
+        j = np.concatenate([j, nb])
+    w = rng.uniform(0.5, 2.0, i.size)
+    W = sp.coo_matrix((np.concatenate([w, w]), (np.concatenate([i, j]), np.concatenate([j, i]))), shape=(n, n)).tocsr()
+    W.sum_duplicates()
+    deg = np.asarray(W.sum(axis=1)).ravel()
+    A = (sp.diags(deg + shift) - W).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return CSR(A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))
+
+
 def sine_mode_2d(N: int, j1: int, j2: int) -> np.ndarray:
     """Discrete sine mode sin(j1 pi x/(N+1)) sin(j2 pi y/(N+1)) on the N x N grid, x fastest."""
     g = np.arange(1, N + 1, dtype=np.float64)

@@ -73,3 +73,19 @@ def test_generators_are_deterministic():
     B1 = batch_shifted_5pt(4, seed=9)
     B2 = batch_shifted_5pt(4, seed=9)
     assert np.array_equal(B1.val, B2.val) and np.array_equal(B1.b, B2.b)
+
+
+def test_graph_laplacian_rows_and_definiteness():
+    from synthetic import graph_laplacian_csr
+
+    rng = np.random.default_rng(3)
+    A = graph_laplacian_csr(3000, rng, hub_degrees=(127, 20))
+    _check_structure(A)
+    lens = np.diff(A.rowptr)
+    hubs = [3000 // 3, 2 * 3000 // 3]
+    assert lens[hubs[0]] == 128 and lens[hubs[1]] == 21 and (lens == 1).any()
+    D = A.to_dense()
+    assert np.allclose(D, D.T)
+    # diagonally dominant by the shift: every row sum is exactly the shift
+    assert np.allclose(D.sum(axis=1), 1.0)
+    assert np.linalg.eigvalsh(D).min() > 0.999
