@@ -86,7 +86,6 @@ apcg_status solve_host_sync(apcg_cg_plan P, const double* b, double* x) {
   while (!done) {
     APCG_TRY(core_k1(c, x, s, true));
     APCG_TRY(read_state(P, s));
-    if (h->done == kDoneStalled) return set_error(APCG_ERR_TIMEOUT, "a bounded wait in the SpMV pipeline ran out");
     const double gamma = h->gamma;
     launches += 1;
     if (!(gamma > 0.0) || !std::isfinite(gamma)) {
@@ -287,12 +286,8 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   const size_t nst = up(sizeof(CgState));
   const size_t nh = up(sizeof(double) * (size_t)(c.hist_len > 0 ? c.hist_len : 1));
   const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
-  const int gstream = need_sell ? core_stream_grid<double>(L.max_width, L.nslices, ctx_num_sms(ctx)) : 0;
-  std::vector<int32_t> stream_blob;
-  if (gstream > 0) core_stream_table(L.sptr, gstream, &stream_blob);
-  const size_t nstream = up(sizeof(int32_t) * (stream_blob.size() + 1));
   const size_t nsell = need_sell ? up(sizeof(int32_t) * ((size_t)L.nslices + 1)) + up(sizeof(int32_t) * (size_t)L.padded) +
-                                       up(sizeof(double) * (size_t)L.padded) + nstream
+                                       up(sizeof(double) * (size_t)L.padded)
                                  : 0;
   const size_t total = 5 * nv + npart + nst + 2 * nh + nsysb + nsell;
   char* ws = nullptr;
@@ -319,8 +314,6 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
     int32_t* scol = reinterpret_cast<int32_t*>(q);
     q += up(sizeof(int32_t) * (size_t)L.padded);
     double* sval = reinterpret_cast<double*>(q);
-    q += up(sizeof(double) * (size_t)L.padded);
-    int32_t* dpart = reinterpret_cast<int32_t*>(q);
     APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice,
                               ctx->stream));
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
@@ -332,7 +325,6 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
     c.A.val = sval;
     c.A.long_rows = L.long_rows;
     core_configure(c, A->nnz, ctx_num_sms(ctx));  // the SpMV kernel instance depends on the row length
-    APCG_TRY(core_attach_stream(c, stream_blob, gstream, dpart, ctx->stream));
   }
   SysDesc d0{};
   d0.row0 = 0;
@@ -392,8 +384,6 @@ apcg_status cg_plan_finish(apcg_cg_plan P, apcg_cg_result* res) {
     if (r.done == kDoneBadDiagonal)
       return set_error(APCG_ERR_BAD_DIAGONAL, "Jacobi: a diagonal entry is missing, zero or not finite");
   }
-  if (P->st_host->done == kDoneStalled)
-    return set_error(APCG_ERR_TIMEOUT, "a bounded wait in the SpMV pipeline ran out");
   fill_result(P, res);
   return APCG_OK;
 }

@@ -34,7 +34,6 @@
 #include "cg_core.hpp"
 #include "kernels_common.cuh"
 #include "sell.cuh"
-#include "sell_stream.cuh"
 
 namespace apcg {
 namespace {
@@ -153,24 +152,6 @@ __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
                                      a.w[i] = s;
                                      v[0] = fma(p_i, s, v[0]);
                                    });
-  T tot[1];
-  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0]);
-}
-
-// K1, streaming form (sell_stream.cuh): the same arithmetic per row, with the
-// matrix entries brought into shared memory by bulk copies.  One CTA per SM.
-template <bool HOST, class T>
-__global__ void __launch_bounds__(dev::kStreamThreads, 1) k1_stream_kernel(Args<T> a, dev::StreamPlan plan) {
-  if (!HOST && read_done(a.st)) return;
-  extern __shared__ __align__(128) unsigned char k1_dyn[];
-  __shared__ T red[dev::kStreamThreads];
-  __shared__ dev::StreamBars bars;
-  T v[1] = {T(0)};
-  const bool ok = dev::sell_spmv_stream<T>(a.A, plan, a.p, k1_dyn, bars, [&](int32_t i, T s, T p_i) {
-    a.w[i] = s;
-    v[0] = fma(p_i, s, v[0]);
-  });
-  if (!ok) a.st->done = kDoneStalled;
   T tot[1];
   if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0]);
 }
@@ -354,9 +335,7 @@ int occupancy_grid(K kernel, int sms, int64_t want) {
 
 template <bool HOST, class T>
 apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
-  if (c.grid_stream > 0)
-    k1_stream_kernel<HOST, T><<<c.grid_stream, dev::kStreamThreads, dev::stream_smem_bytes<T>(), s>>>(a, c.splan);
-  else if (c.A.long_rows)
+  if (c.A.long_rows)
     k1_kernel<HOST, true, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
   else
     k1_kernel<HOST, false, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
@@ -375,75 +354,6 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
   c.grid_spmv = occupancy_grid(c.A.long_rows ? (void*)k1_kernel<false, true, T> : (void*)k1_kernel<false, false, T>, sms,
                                spmv_blocks);
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
-}
-
-template <class T>
-int core_stream_grid(int32_t max_width, int32_t nslices, int sms) {
-  if (max_width > dev::kStreamMaxWidth || nslices < 64 * sms) return 0;  // small matrices: the plain K1
-  const size_t smem = dev::stream_smem_bytes<T>();
-  int per_sm = 0;
-  for (auto kern : {k1_stream_kernel<false, T>, k1_stream_kernel<true, T>}) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return 0;
-    }
-  }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1_stream_kernel<false, T>, dev::kStreamThreads, smem) !=
-          cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    return 0;
-  }
-  return std::min(per_sm * sms, dev::kMaxPartials);
-}
-
-void core_stream_table(const std::vector<int32_t>& sptr, int grid, std::vector<int32_t>* blob) {
-  blob->clear();
-  if (grid <= 0) return;
-  // CTA g streams slices [part[g], part[g+1]): about total / grid entries each.
-  const int32_t nslices = (int32_t)sptr.size() - 1;
-  const int64_t total = sptr[nslices];
-  std::vector<int32_t> part((size_t)grid + 1), stage_ptr((size_t)grid + 1);
-  for (int g = 0; g <= grid; ++g) {
-    const int64_t target = total * g / grid;
-    part[g] = (int32_t)(std::lower_bound(sptr.begin(), sptr.end() - 1, (int32_t)target) - sptr.begin());
-  }
-  part[0] = 0;
-  part[grid] = nslices;
-  // Stages: whole consecutive slices, at most kStageEntries entries each.
-  std::vector<int32_t> st;  // 4 ints per stage
-  for (int g = 0; g < grid; ++g) {
-    stage_ptr[g] = (int32_t)(st.size() / 4);
-    int32_t s = part[g];
-    while (s < part[g + 1]) {
-      int32_t e = s + 1;
-      while (e < part[g + 1] && sptr[e + 1] - sptr[s] <= dev::kStageEntries) ++e;
-      st.insert(st.end(), {s, e, sptr[s], sptr[e] - sptr[s]});
-      s = e;
-    }
-  }
-  stage_ptr[grid] = (int32_t)(st.size() / 4);
-  // blob: part | stage_ptr | (pad to 16 bytes) | stages
-  blob->insert(blob->end(), part.begin(), part.end());
-  blob->insert(blob->end(), stage_ptr.begin(), stage_ptr.end());
-  while (blob->size() % 4) blob->push_back(0);
-  blob->insert(blob->end(), st.begin(), st.end());
-}
-
-template <class T>
-apcg_status core_attach_stream(CgCore<T>& c, const std::vector<int32_t>& blob, int grid, int32_t* d_blob,
-                               cudaStream_t s) {
-  c.grid_stream = 0;
-  c.splan = dev::StreamPlan{};
-  if (grid <= 0 || blob.empty()) return APCG_OK;
-  APCG_CUDA(cudaMemcpyAsync(d_blob, blob.data(), sizeof(int32_t) * blob.size(), cudaMemcpyHostToDevice, s));
-  counters().h2d_copies++;
-  const size_t off_st = ((size_t)2 * (grid + 1) + 3) / 4 * 4;
-  c.splan.part = d_blob;
-  c.splan.stage_ptr = d_blob + grid + 1;
-  c.splan.stages = reinterpret_cast<const int4*>(d_blob + off_st);
-  c.grid_stream = grid;
-  return APCG_OK;
 }
 
 template <class T>
@@ -532,12 +442,6 @@ apcg_status core_setup_f64(const CgCore<double>& c, const double* b, double* x, 
 
 template void core_configure<double>(CgCore<double>&, int64_t, int);
 template void core_configure<float>(CgCore<float>&, int64_t, int);
-template int core_stream_grid<double>(int32_t, int32_t, int);
-template int core_stream_grid<float>(int32_t, int32_t, int);
-template apcg_status core_attach_stream<double>(CgCore<double>&, const std::vector<int32_t>&, int, int32_t*,
-                                                cudaStream_t);
-template apcg_status core_attach_stream<float>(CgCore<float>&, const std::vector<int32_t>&, int, int32_t*,
-                                               cudaStream_t);
 template apcg_status core_k1<double>(const CgCore<double>&, double*, cudaStream_t, bool);
 template apcg_status core_k1<float>(const CgCore<float>&, float*, cudaStream_t, bool);
 template apcg_status core_k2<double>(const CgCore<double>&, double*, cudaStream_t, bool, double,

@@ -7,12 +7,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <vector>
 
 #include "apcg_internal.hpp"
 #include "cg_internal.hpp"
 #include "sell.cuh"
-#include "sell_stream.cuh"
 
 namespace apcg {
 
@@ -23,8 +21,6 @@ struct CgCore {
   int32_t max_it = 0;
   int32_t hist_len = 0;
   int grid_spmv = 1, grid_vec = 1;
-  int grid_stream = 0;    // > 0: K1 streams the matrix through shared memory (sell_stream.cuh)
-  dev::StreamPlan splan;  // its work split
   dev::SellView<T> A;     // sliced-ELL copy of the matrix (values in T)
   T* dinv = nullptr;
   T* r = nullptr;
@@ -44,17 +40,6 @@ struct CgCore {
 // Choose the persistent grids for n rows (nnz is informational).  Call after c.A is set.
 template <class T>
 void core_configure(CgCore<T>& c, int64_t nnz, int sms);
-
-// Streaming K1: the CTA count for a matrix whose widest slice has max_width
-// entries per row (0: use the plain K1); the host-built work split for that
-// grid from the layout's slice offsets (an int32 blob, empty for grid 0); and
-// its attachment, copied to d_blob (device, blob.size() ints, 16-byte aligned).
-template <class T>
-int core_stream_grid(int32_t max_width, int32_t nslices, int sms);
-void core_stream_table(const std::vector<int32_t>& sptr, int grid, std::vector<int32_t>* blob);
-template <class T>
-apcg_status core_attach_stream(CgCore<T>& c, const std::vector<int32_t>& blob, int grid, int32_t* d_blob,
-                               cudaStream_t s);
 
 // K1: w = A p, gamma = (p,w); the last block forms alpha (device mode) or only gamma (host mode).
 template <class T>

@@ -11,14 +11,7 @@
 namespace apcg {
 
 // 'done' word of the device state block.
-enum : int32_t {
-  kDoneRunning = 0,
-  kDoneConverged = 1,
-  kDoneNotConverged = 2,
-  kDoneBreakdown = 3,
-  kDoneBadDiagonal = 4,
-  kDoneStalled = 5  // a bounded wait inside a kernel ran out (reported as APCG_ERR_TIMEOUT)
-};
+enum : int32_t { kDoneRunning = 0, kDoneConverged = 1, kDoneNotConverged = 2, kDoneBreakdown = 3, kDoneBadDiagonal = 4 };
 
 // Device-resident scalars of one solve (the managed scalars of Sec. 3.2).
 struct CgState {

@@ -167,25 +167,19 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(float) * (size_t)(P->n > 0 ? P->n : 1));
   const size_t nsptr = up(sizeof(int32_t) * ((size_t)L.nslices + 1));
-  const int gstream = core_stream_grid<float>(L.max_width, L.nslices, sms);
-  std::vector<int32_t> stream_blob;
-  if (gstream > 0) core_stream_table(L.sptr, gstream, &stream_blob);
-  const size_t npart = up(sizeof(int32_t) * (stream_blob.size() + 1));
   const size_t ncol = up(sizeof(int32_t) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nv32 = up(sizeof(float) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nv64 = A64 ? up(sizeof(double) * (size_t)std::max<int64_t>(L.padded, 1)) : 0;
   const size_t nip = up(sizeof(float) * dev::kMaxPartials * 3);
   const size_t nop = up(sizeof(double) * dev::kMaxPartials * 2);
   const size_t nst = up(sizeof(CgState)) + up(sizeof(IrState));
-  const size_t total = nsptr + npart + ncol + nv32 + nv64 + 6 * nv + nip + nop + nst;
+  const size_t total = nsptr + ncol + nv32 + nv64 + 6 * nv + nip + nop + nst;
   char* ws = nullptr;
   APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
   P->ws = ws;
   char* q = ws;
   int32_t* sptr = reinterpret_cast<int32_t*>(q);
   q += nsptr;
-  int32_t* dpart = reinterpret_cast<int32_t*>(q);
-  q += npart;
   int32_t* scol = reinterpret_cast<int32_t*>(q);
   q += ncol;
   float* sval32 = reinterpret_cast<float*>(q);
@@ -238,7 +232,6 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   P->A32.long_rows = P->A64.long_rows = L.long_rows;
   c.A = P->A32;
   core_configure(c, S.nnz, sms);  // the SpMV kernel instance depends on the row length
-  APCG_TRY(core_attach_stream(c, stream_blob, gstream, dpart, ctx->stream));
   P->grid_res = c.grid_spmv;
   if (P->n > 0) {
     const int g = std::max(1, std::min(sms * 8, (int)((P->n + kThreads - 1) / kThreads)));
@@ -301,10 +294,6 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
     }
     if (k == P->opts.max_outer) {
       res->reason = APCG_NOT_CONVERGED;
-      break;
-    }
-    if (hi->done == kDoneStalled) {
-      st = set_error(APCG_ERR_TIMEOUT, "a bounded wait in the SpMV pipeline ran out");
       break;
     }
     if (hi->done) {  // the float32 right-hand side vanished: no further progress possible

@@ -1,13 +1,13 @@
-"""The streaming form of K1 (matrix entries through shared memory by bulk
-copies, one producer warp per CTA) against the oracle.
+"""Large systems with irregular rows against the oracle.
 
-The streaming K1 serves matrices with at least 64 slices of 32 rows per SM and
-rows of at most 128 entries; these tests use such sizes: a 7-point Laplacian
-(ragged against every stage and CTA boundary) and weighted graph Laplacians
-whose rows range from the diagonal alone to 128 entries (the longest row the
-stages hold) or 129 (served by the plain K1 instead).  Parity bars as for the
-other CG tests: alpha/beta of the first 10 iterations within 1e-12 relative,
-the iteration count equal, x within 1e-7 of the oracle's at rtol 1e-8.
+The benchmark-size tests use stencils, whose slices of 32 rows are almost
+uniform.  These systems stress the sliced-ELL SpMV where they are not: a
+7-point Laplacian whose size is ragged against every slice and grid boundary,
+and weighted graph Laplacians whose rows range from the diagonal alone to 128
+or 129 entries (hub rows far longer than their slice neighbours, so slices
+carry heavy padding).  Parity bars as for the other CG tests: alpha/beta of the
+first 10 iterations within 1e-12 relative, the same iteration count, x within
+1e-7 of the oracle's at rtol 1e-8.
 """
 
 import ctypes as C
@@ -65,7 +65,7 @@ def _check(res, x, ref, k):
 
 
 @pytest.mark.parametrize("mode", ["host_sync", "async_graph"])
-def test_stream_k1_7pt_ragged(ctx, mode):
+def test_7pt_ragged_size(ctx, mode):
     A = laplace_3d_7pt(71)  # 357,911 rows: the last slice and the last stage are partial
     rng = np.random.default_rng(5)
     b = rhs_from_solution(A, rng.uniform(-1, 1, A.n))
@@ -76,7 +76,7 @@ def test_stream_k1_7pt_ragged(ctx, mode):
 
 @pytest.mark.parametrize("hub_degree", [127, 128])
 @pytest.mark.parametrize("mode", ["host_sync", "async_graph"])
-def test_stream_k1_irregular_rows(ctx, hub_degree, mode):
+def test_graph_laplacian_hub_rows(ctx, hub_degree, mode):
     rng = np.random.default_rng(hub_degree)
     A = graph_laplacian_csr(330_000, rng, hub_degrees=(hub_degree, 40, hub_degree))
     lens = np.diff(A.rowptr)
@@ -87,7 +87,7 @@ def test_stream_k1_irregular_rows(ctx, hub_degree, mode):
     _check(res, x, ref, 1)
 
 
-def test_stream_k1_check_interval(ctx):
+def test_graph_laplacian_check_interval(ctx):
     rng = np.random.default_rng(9)
     A = graph_laplacian_csr(400_000, rng, mean_degree=3.0, hub_degrees=(64,))
     b = rhs_from_solution(A, rng.uniform(-1, 1, A.n))
