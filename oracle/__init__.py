@@ -1,4 +1,4 @@
-"""CPU oracle for the Jacobi-preconditioned CG path (test infrastructure).
+"""CPU oracle for the Jacobi-preconditioned CG and TFQMR paths (test infrastructure).
 
 Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 leg may import this package.  The product path never does; it shares no code
@@ -13,6 +13,7 @@ from .oracle import (  # noqa: F401
     spmv,
     diagonal,
     pcg,
+    tfqmr,
     pcg_f32,
     ir,
 )

@@ -1,4 +1,4 @@
-"""ctypes front end of the plain C oracle (``pcg_oracle.c``).
+"""ctypes front end of the plain C oracle (``pcg_oracle.c``, ``tfqmr_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: only the tests, the smoke check and the benchmark's
 CPU-baseline leg may use it.  The library is compiled with gcc (ISO C11,
@@ -6,8 +6,8 @@ CPU-baseline leg may use it.  The library is compiled with gcc (ISO C11,
 the same bits) into ``oracle/_build``.
 
 Every function takes numpy arrays and returns numpy arrays; see the C file for
-the algorithm (textbook Jacobi-PCG, Sec. 4.1-4.2, loop order of the mixed-API
-example of Sec. 3.3).
+the algorithms (textbook Jacobi-PCG, Sec. 4.1-4.2, loop order of the mixed-API
+example of Sec. 3.3; Jacobi-preconditioned TFQMR, Sec. 4.3).
 """
 
 from __future__ import annotations
@@ -20,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "pcg_oracle.c")
+_SRCS = [os.path.join(_HERE, "pcg_oracle.c"), os.path.join(_HERE, "tfqmr_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -31,6 +31,16 @@ REASON = {0: "converged", 1: "not_converged", 2: "breakdown", 3: "bad_diagonal",
 
 class _Res(C.Structure):
     _fields_ = [("iters", C.c_int32), ("reason", C.c_int32), ("rr", C.c_double), ("bnorm", C.c_double)]
+
+
+class _TqRes(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32),
+        ("reason", C.c_int32),
+        ("tau", C.c_double),
+        ("bound", C.c_double),
+        ("bnorm", C.c_double),
+    ]
 
 
 class _IrRes(C.Structure):
@@ -46,9 +56,9 @@ class _IrRes(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle shared library if it is missing or older than its source."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -78,6 +88,8 @@ def load():
             lib.oracle_pcg_f32.restype = C.c_int
             lib.oracle_ir.argtypes = [i64, P, P, P, P, P, P, f64, i32, f32, i32, i32, C.POINTER(_IrRes)]
             lib.oracle_ir.restype = C.c_int
+            lib.oracle_tfqmr.argtypes = [i64, P, P, P, P, P, f64, f64, i32, i32, i32, P, P, P, i32, C.POINTER(_TqRes)]
+            lib.oracle_tfqmr.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -144,6 +156,29 @@ def pcg(A, b, x0=None, rtol=1e-8, atol=0.0, max_it=None, check_every=1, hist_len
         _p(hs["alpha"]), _p(hs["beta"]), _p(hs["gamma"]), _p(hs["rho"]), _p(hs["rr_hist"]), int(mutation), C.byref(res),
     )
     out = dict(x=x, iters=int(res.iters), reason=REASON[res.reason], rr=float(res.rr), bnorm=float(res.bnorm))
+    for k, v in hs.items():
+        out[k] = v[:H]
+    return out
+
+
+def tfqmr(A, b, x0=None, rtol=1e-8, atol=0.0, max_it=None, check_every=1, hist_len=0, mutation=0) -> dict:
+    """Jacobi-preconditioned (left) TFQMR in float64.  Returns x, iters, reason, tau, bound, bnorm
+    (norms of the preconditioned system) and the alpha, beta and tau_hist histories."""
+    rowptr, col, val = _csr(A)
+    n = A.n
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n, dtype=np.float64) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    if max_it is None:
+        max_it = max(10 * n, 10)
+    H = int(hist_len)
+    hs = {k: np.full(max(H, 1), np.nan) for k in ("alpha", "beta", "tau_hist")}
+    res = _TqRes()
+    load().oracle_tfqmr(
+        n, _p(rowptr), _p(col), _p(val), _p(b), _p(x), float(rtol), float(atol), int(max_it), int(check_every), H,
+        _p(hs["alpha"]), _p(hs["beta"]), _p(hs["tau_hist"]), int(mutation), C.byref(res),
+    )
+    out = dict(x=x, iters=int(res.iters), reason=REASON[res.reason], tau=float(res.tau), bound=float(res.bound),
+               bnorm=float(res.bnorm))
     for k, v in hs.items():
         out[k] = v[:H]
     return out

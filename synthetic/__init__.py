@@ -21,6 +21,7 @@ from .stencils import (  # noqa: F401
     diagonal_csr,
     random_spd_csr,
     graph_laplacian_csr,
+    convection_diffusion_2d,
     sine_mode_2d,
     sine_mode_3d,
     rhs_from_solution,

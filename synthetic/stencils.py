@@ -206,6 +206,28 @@ def random_spd_csr(n: int, density: float, rng: np.random.Generator, dominance: 
     return CSR(m.indptr.astype(np.int32), m.indices.astype(np.int32), m.data.astype(np.float64))
 
 
+def convection_diffusion_2d(N: int, gx: float, gy: float, shift: float = 0.0) -> CSR:
+    """Nonsymmetric 5-point convection-diffusion operator on an N x N grid (Dirichlet, unscaled).
+
+    Central differences: diagonal 4 + shift, west/east couplings -1 -/+ gx,
+    south/north -1 -/+ gy (gx, gy are the cell Peclet numbers over two).  For
+    |gx|, |gy| < 1 every off-diagonal is negative and the matrix is a
+    nonsingular M-matrix; it is symmetric only for gx = gy = 0.
+    """
+    n = N * N
+    idx = np.arange(n, dtype=np.int64)
+    ix, iy = idx % N, idx // N
+    rows, cols, vals = [idx], [idx], [np.full(n, 4.0 + shift)]
+    for dx, dy, v in ((-1, 0, -1.0 - gx), (1, 0, -1.0 + gx), (0, -1, -1.0 - gy), (0, 1, -1.0 + gy)):
+        ok = (ix + dx >= 0) & (ix + dx < N) & (iy + dy >= 0) & (iy + dy < N)
+        rows.append(idx[ok])
+        cols.append(idx[ok] + dx + dy * N)
+        vals.append(np.full(int(ok.sum()), v))
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
+    A.sort_indices()
+    return CSR(A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))
+
+
 def graph_laplacian_csr(n: int, rng: np.random.Generator, mean_degree: float = 6.0, hub_degrees=(),
                         shift: float = 1.0) -> CSR:
     """Weighted graph Laplacian of a random graph plus shift * I (symmetric positive definite).
