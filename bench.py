@@ -434,8 +434,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="only the set-up and 3 iterations, kernels launched one by one (for profilers)")
-    ap.add_argument("--config", choices=["c2", "c3", "c4", "c5"], default="c2",
-                    help="c2: the headline 128^3 workload (default); c3/c4/c5: extra measurement lines")
+    ap.add_argument("--config", choices=["c2", "c3", "c4", "c5", "tfqmr"], default="c2",
+                    help="c2: the headline 128^3 workload (default); c3/c4/c5/tfqmr: extra measurement lines")
     ap.add_argument("--no-tune", action="store_true", help="c4/c5: skip the batched autotuner")
     args = ap.parse_args()
     rank, world, local = _env_rank()
@@ -457,7 +457,7 @@ def main():
         ncu_case()
         return
     if args.config != "c2":
-        {"c3": bench_c3, "c4": bench_c4, "c5": bench_c5}[args.config](args)
+        {"c3": bench_c3, "c4": bench_c4, "c5": bench_c5, "tfqmr": bench_tfqmr}[args.config](args)
         return
     run_apcg(args, rank, world, local)
 
@@ -694,6 +694,54 @@ def bench_c5(args):
     out["max_rel_err_vs_fp64_batched"] = float(err_64)
     line = {"metric": "batched mixed-precision solves/s at rtol 1e-10", "value": B.nsys / dt_ir, "unit": "solves/s",
             "dtype": "f32+f64", "data": "synthetic", **out}
+    print(json.dumps(line), flush=True)
+
+
+def bench_tfqmr(args):
+    """Jacobi-TFQMR (Sec. 4.3) on the 64^2 5-point and 128^3 7-point systems: host-synchronous vs
+    asynchronous forms, microseconds per iteration (two SpMVs each)."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+    from synthetic import single_problem
+
+    V = C.c_void_p
+    dev = torch.device("cuda", 0)
+    apcg.load()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = apcg.ctx_create(stream)
+    out = {"config": {"workload": "Jacobi-TFQMR to rtol 1e-8 on 2D 5-point 64^2 (k=1) and 3D 7-point 128^3 (k=10)"}}
+    for cfg, k in (("c1", 1), ("c2", 10)):
+        p = single_problem(cfg, seed=0)
+        g = _gpu_problem(p, dev)
+        row = {"n": p.n, "nnz": p.nnz, "k": k}
+        for mode in ("host_sync", "async", "async_graph"):
+            plan = apcg.tfqmr_plan_create(ctx, g["A"], apcg.cg_opts(rtol=1e-8, check_every=k, mode=mode, max_it=20000))
+            best, r = None, None
+            for i in range(max(2, args.steps // 3) + 1):
+                apcg.call("apcg_vec_set_async", V(ctx), V(g["vx"]), C.c_double(0.0))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = apcg.tfqmr_plan_solve(plan, g["vb"], g["vx"])
+                dt = time.perf_counter() - t0
+                if i > 0:
+                    best = dt if best is None else min(best, dt)
+            apcg.call("apcg_tfqmr_plan_destroy", V(plan))
+            assert r["reason"] == "converged"
+            row[mode] = {"ms_per_solve": 1e3 * best, "iters": r["iters"], "us_per_iteration": 1e6 * best / r["iters"],
+                         "kernel_launches": r["kernel_launches"]}
+        row["speedup_async_graph_vs_host_sync"] = row["host_sync"]["ms_per_solve"] / row["async_graph"]["ms_per_solve"]
+        b_it = 24 * p.nnz + 8 * (p.n + 1) + 232 * p.n
+        row["algorithmic_bytes_per_iteration"] = b_it
+        row["GBps_per_iteration"] = b_it / (1e-6 * row["async_graph"]["us_per_iteration"]) / 1e9
+        out[cfg] = row
+        for h, fn in ((g["vb"], "apcg_vec_destroy"), (g["vx"], "apcg_vec_destroy"), (g["A"], "apcg_mat_destroy")):
+            apcg.call(fn, V(h))
+    line = {"metric": "TFQMR us/iteration and solves/s at rtol 1e-8 (async vs host-sync, FP64)",
+            "value": 1e3 / out["c2"]["async_graph"]["ms_per_solve"], "unit": "solves/s", "dtype": "f64",
+            "data": "synthetic", **out}
     print(json.dumps(line), flush=True)
 
 

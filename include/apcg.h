@@ -473,6 +473,43 @@ APCG_API apcg_status apcg_ir_plan_destroy(apcg_ir_plan plan);
 APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
                                    const apcg_ir_opts* opts, apcg_ir_result* res);
 
+/* ------------------------------------------------------------------ TFQMR */
+
+/*
+ * Transpose-free quasi-minimal residual (Freund 1993), the paper's second
+ * solver (Sec. 4.3: two matrix-vector products and about twice the inner
+ * products of a CG iteration; for nonsymmetric and indefinite systems too),
+ * with the Jacobi preconditioner applied on the left: the method runs on
+ * M = D^-1 A and D^-1 b, D = diag(A), with the shadow residual r* = r0.
+ *
+ * A: square float64 CSR with a nonzero diagonal (need not be symmetric).
+ * b, x: device float64 [n], 16-byte aligned; x holds x0 on entry and the
+ * iterate on exit.  Marks A and b read, x read-write.
+ *
+ * opts (apcg_cg_opts): rtol, atol, max_it (<= 0: 10 n), check_every k, mode
+ * (HOST_SYNC, ASYNC; ASYNC_GRAPH for AUTO/PERSISTENT/ASYNC_GRAPH), history.
+ * Convergence test, every k iterations and at max_it: Freund's bound
+ * sqrt(2i + 1) tau_i <= max(rtol ||D^-1 b||, atol), tau_i the quasi-residual
+ * norm after iteration i (two half-steps); a quasi-residual of exactly zero
+ * stops at once.  alpha_hist[i-1] receives alpha of iteration i, beta_hist[i-1]
+ * the beta formed at its end.
+ *
+ * Result (apcg_cg_result): iters, reason, rr = (sqrt(2 iters + 1) tau)^2 (the
+ * bound, squared), bnorm = ||D^-1 b||, rel_res = bound / bnorm.  Returns
+ * APCG_ERR_BAD_DIAGONAL for a zero, missing or non-finite diagonal entry
+ * (at plan creation); a breakdown ((v, r*) = 0, (r*, w) = 0 or a non-finite
+ * scalar) or the iteration cap is reported in res->reason.
+ */
+typedef struct apcg_tfqmr_plan_s* apcg_tfqmr_plan;
+APCG_API apcg_status apcg_tfqmr_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts,
+                                            apcg_tfqmr_plan* out);
+/* Solve with a plan; blocks until the solve ends. */
+APCG_API apcg_status apcg_tfqmr_plan_solve(apcg_tfqmr_plan plan, apcg_vec b, apcg_vec x, apcg_cg_result* res);
+APCG_API apcg_status apcg_tfqmr_plan_destroy(apcg_tfqmr_plan plan);
+/* One-shot form of create + solve + destroy. */
+APCG_API apcg_status apcg_tfqmr_solve(apcg_ctx ctx, apcg_mat A, apcg_vec b, apcg_vec x, const apcg_cg_opts* opts,
+                                      apcg_cg_result* res);
+
 /* ------------------------------------------------------------------ batched solves (many independent systems) */
 
 /*

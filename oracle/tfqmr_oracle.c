@@ -80,9 +80,10 @@ static int half_step_end(int64_t n, const double* w, double alpha, double* theta
   const double c = 1.0 / sqrt(1.0 + (*theta) * (*theta));
   *tau = (*tau) * (*theta) * c;
   *eta = c * c * alpha;
+  if (!isfinite(*theta) || !isfinite(*tau)) return 0; /* breakdown: x keeps the last finite iterate */
   if (!skip_x)
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] + (*eta) * dv[i];
-  return isfinite(*theta) && isfinite(*tau);
+  return 1;
 }
 
 /*

@@ -215,6 +215,10 @@ PROTOS = {
     "apcg_ir_plan_solve": [P, P, P, C.POINTER(IrResult)],
     "apcg_ir_plan_destroy": [P],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
+    "apcg_tfqmr_plan_create": [P, P, C.POINTER(CgOpts), PP],
+    "apcg_tfqmr_plan_solve": [P, P, P, C.POINTER(CgResult)],
+    "apcg_tfqmr_plan_destroy": [P],
+    "apcg_tfqmr_solve": [P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
     "apcg_batch_plan_create": [P, i32, P, P, P, P, C.POINTER(CgOpts), PP],
     "apcg_batch_ir_plan_create": [P, i32, P, P, P, P, P, C.POINTER(IrOpts), PP],
     "apcg_batch_plan_solve": [P, P, P, P],
@@ -451,6 +455,29 @@ def cg_solve_host(rowptr, col, val, b, x, opts: CgOpts) -> dict:
         C.byref(opts),
         C.byref(res),
     )
+    return res.as_dict()
+
+
+def tfqmr_solve(ctx, A, b, x, opts: CgOpts) -> dict:
+    """Jacobi-preconditioned TFQMR (apcg_vec/apcg_mat handles)."""
+    res = CgResult()
+    call("apcg_tfqmr_solve", C.c_void_p(ctx), C.c_void_p(A), C.c_void_p(b), C.c_void_p(x), C.byref(opts), C.byref(res))
+    out = res.as_dict()
+    if opts.history_len:
+        out["alpha"] = list(opts._hist[0])
+        out["beta"] = list(opts._hist[1])
+    return out
+
+
+def tfqmr_plan_create(ctx, A, opts: CgOpts):
+    h = _out()
+    call("apcg_tfqmr_plan_create", C.c_void_p(ctx), C.c_void_p(A), C.byref(opts), C.byref(h))
+    return h.value
+
+
+def tfqmr_plan_solve(plan, b, x) -> dict:
+    res = CgResult()
+    call("apcg_tfqmr_plan_solve", C.c_void_p(plan), C.c_void_p(b), C.c_void_p(x), C.byref(res))
     return res.as_dict()
 
 

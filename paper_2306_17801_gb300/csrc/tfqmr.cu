@@ -1,0 +1,866 @@
+// Jacobi-preconditioned TFQMR (Sec. 4.3) on one device context (float64).
+//
+// Freund's transpose-free QMR, two half-steps per iteration, with the Jacobi
+// preconditioner on the left: the operator is M = D^-1 A and the right-hand
+// side D^-1 b.  Shadow residual r* = r0.  Per iteration (the half-steps of
+// the method, grouped into three kernels that end at its three reductions):
+//
+//   T1 (odd half-step)   x += eta_x d (the previous half-step's update, pending)
+//                        u2 = u - alpha v;  w -= alpha p;  d = u + co d;  ||w||^2
+//                        last block: theta = ||w|| / tau;  c = (1 + theta^2)^-1/2;
+//                                    tau *= theta c;  eta = c^2 alpha;  co = theta^2 eta / alpha
+//   T2 (even half-step)  q = M u2 (SpMV);  x += eta_x d;  w -= alpha q;  d = u2 + co d;
+//                        ||w||^2, (w, r*)
+//                        last block: theta, tau, eta as above; the convergence test
+//                                    sqrt(2i + 1) tau <= tol every k iterations;
+//                                    beta = (w, r*) / rho;  rho = (w, r*)
+//   T3 (directions)      u = w + beta u2;  p = M u = M w + beta q (SpMV of w);
+//                        v = p + beta (q + beta v);  (v, r*)
+//                        last block: alpha = rho / (v, r*);  co = theta^2 eta / alpha
+//
+// p = M u is written as M w + beta M u2 (linearity), so that T3 needs the SpMV
+// of w, which is complete when T2 ends, instead of that of u, which T3
+// itself produces; it saves a kernel and a grid-wide boundary per iteration
+// and changes only the rounding.  The update x += eta d of a half-step needs
+// eta from that half-step's reduction, so it is applied by the next kernel
+// that rewrites d (or, when the solve stops, by a finish kernel).
+//
+// An iteration reads the matrix twice (two SpMVs) and reduces four inner
+// products at three points, against one SpMV and two or three products for
+// CG (Sec. 4.3).  The solve modes are those of the CG plan: HOST_SYNC (every
+// reduction read by the host, scalars passed by value), ASYNC (host reads the
+// done word every k iterations) and ASYNC_GRAPH (k iterations in the body of
+// a conditional while node).  AUTO and PERSISTENT select ASYNC_GRAPH.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "apcg_internal.hpp"
+#include "cg_internal.hpp"
+#include "kernels_common.cuh"
+#include "sell.cuh"
+#include "sell.hpp"
+
+namespace apcg {
+namespace tq {
+
+constexpr int kThreads = 256;
+
+// Device-resident scalars of one TFQMR solve.
+struct TqState {
+  double rho;      // (r*, w) of the last direction update (rho_1 = (r*, r0))
+  double alpha, beta, theta, eta, tau;
+  double co;       // coefficient of d in the next half-step: theta^2 eta / alpha
+  double eta_x;    // pending update x += eta_x d
+  double tol;      // max(rtol ||D^-1 b||, atol)
+  double bnorm2;   // ||D^-1 b||^2
+  double ww, wr, sigma;  // last reductions (read by the host in the host-synchronous form)
+  int32_t iter;    // completed iterations
+  int32_t done;    // kDone*
+  int32_t max_it, check_every, hist_len;
+  int32_t pending;  // eta_x holds an update not yet applied to x
+  int32_t body_runs;
+  unsigned int ticket;
+};
+
+struct TqArgs {
+  dev::SellView<double> A;
+  int32_t n;
+  const double* __restrict__ dinv;
+  double* rs;  // r*
+  double* x;
+  double* u;
+  double* u2;
+  double* w;
+  double* d;
+  double* v;
+  double* p;
+  double* q;
+  TqState* st;
+  double* partials;
+  double* alpha_h;
+  double* beta_h;
+};
+
+// Scalars passed by value in the host-synchronous form.
+struct HostScalars {
+  double alpha, beta, co, eta_x;
+  int32_t pending;
+};
+
+__device__ __forceinline__ int32_t read_done(const TqState* st) { return *(volatile const int32_t*)&st->done; }
+
+// The quasi-residual update after a half-step (last block, device mode).
+// Returns false on a non-finite value.
+__device__ __forceinline__ bool quasi_update(TqState* st, double ww) {
+  const double theta = sqrt(ww) / st->tau;
+  const double c = 1.0 / sqrt(1.0 + theta * theta);
+  const double tau = st->tau * theta * c;
+  const double eta = c * c * st->alpha;
+  st->theta = theta;
+  st->tau = tau;
+  st->eta = eta;
+  st->eta_x = eta;
+  st->pending = 1;
+  return isfinite(theta) && isfinite(tau);
+}
+
+// S1: r0 = D^-1 (b - A x0);  u = w = r* = r0;  d = 0;  ||r0||^2, ||D^-1 b||^2;
+// tau = ||r0||, rho = (r*, r0), the tolerance and the initial test.
+template <bool LONG>
+__global__ void __launch_bounds__(kThreads) s1_kernel(TqArgs a, const double* __restrict__ b, double rtol,
+                                                      double atol, int32_t max_it, int32_t k, int32_t hist_len) {
+  __shared__ double red[2 * kThreads];
+  double v[2] = {0.0, 0.0};
+  dev::sell_spmv<false, LONG, double>(a.A, a.x, [&](int32_t i, double ax, double) {
+                                           const double di = __ldg(a.dinv + i);
+                                           const double bi = __ldg(b + i);
+                                           const double ri = di * (bi - ax);
+                                           const double bh = di * bi;
+                                           a.u[i] = ri;
+                                           a.w[i] = ri;
+                                           a.rs[i] = ri;
+                                           a.d[i] = 0.0;
+                                           v[0] = fma(ri, ri, v[0]);
+                                           v[1] = fma(bh, bh, v[1]);
+                                         });
+  double tot[2];
+  if (dev::grid_sum_last<2>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    TqState* st = a.st;
+    st->rho = tot[0];
+    st->ww = tot[0];
+    st->bnorm2 = tot[1];
+    st->tau = sqrt(tot[0]);
+    st->tol = fmax(rtol * sqrt(tot[1]), atol);
+    st->theta = st->eta = st->co = st->eta_x = 0.0;
+    st->alpha = st->beta = st->sigma = st->wr = 0.0;
+    st->pending = 0;
+    st->iter = 0;
+    st->max_it = max_it;
+    st->check_every = k;
+    st->hist_len = hist_len;
+    st->body_runs = 0;
+    st->done = st->tau <= st->tol ? kDoneConverged : 0;
+  }
+}
+
+// S2: p = M u;  v = p;  sigma = (v, r*);  alpha = rho / sigma (device mode).
+template <bool HOST, bool LONG>
+__global__ void __launch_bounds__(kThreads) s2_kernel(TqArgs a) {
+  if (!HOST && read_done(a.st)) return;
+  __shared__ double red[kThreads];
+  double v[1] = {0.0};
+  dev::sell_spmv<false, LONG, double>(a.A, a.u, [&](int32_t i, double au, double) {
+                                           const double pi = __ldg(a.dinv + i) * au;
+                                           a.p[i] = pi;
+                                           a.v[i] = pi;
+                                           v[0] = fma(pi, __ldg(a.rs + i), v[0]);
+                                         });
+  double tot[1];
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    TqState* st = a.st;
+    st->sigma = tot[0];
+    if (!HOST) {
+      if (tot[0] == 0.0 || !isfinite(tot[0])) {
+        st->done = kDoneBreakdown;
+      } else {
+        st->alpha = st->rho / tot[0];
+        st->co = 0.0;
+        if (st->hist_len > 0) a.alpha_h[0] = st->alpha;
+      }
+    }
+  }
+}
+
+// T1, the odd half-step (vectors only).
+template <bool HOST>
+__global__ void __launch_bounds__(kThreads, 4) t1_kernel(TqArgs a, HostScalars h) {
+  if (!HOST && read_done(a.st)) return;
+  const double alpha = HOST ? h.alpha : a.st->alpha;
+  const double co = HOST ? h.co : a.st->co;
+  const bool pend = HOST ? h.pending != 0 : a.st->pending != 0;
+  const double ex = HOST ? h.eta_x : a.st->eta_x;
+  __shared__ double red[kThreads];
+  double acc = 0.0;
+  const int64_t n = a.n, nv = n / 2, stride = (int64_t)gridDim.x * blockDim.x;
+  double2* xv = reinterpret_cast<double2*>(a.x);
+  const double2* uv = reinterpret_cast<const double2*>(a.u);
+  const double2* vv = reinterpret_cast<const double2*>(a.v);
+  const double2* pv = reinterpret_cast<const double2*>(a.p);
+  double2* wv = reinterpret_cast<double2*>(a.w);
+  double2* dv = reinterpret_cast<double2*>(a.d);
+  double2* u2v = reinterpret_cast<double2*>(a.u2);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const double2 uu = dev::ld_stream2(uv + i), vvv = dev::ld_stream2(vv + i), pp = dev::ld_stream2(pv + i);
+    double2 ww = wv[i], dd = dv[i], u2;
+    if (pend) {
+      double2 xx = xv[i];
+      xx.x = fma(ex, dd.x, xx.x);
+      xx.y = fma(ex, dd.y, xx.y);
+      xv[i] = xx;
+    }
+    u2.x = fma(-alpha, vvv.x, uu.x);
+    u2.y = fma(-alpha, vvv.y, uu.y);
+    ww.x = fma(-alpha, pp.x, ww.x);
+    ww.y = fma(-alpha, pp.y, ww.y);
+    dd.x = fma(co, dd.x, uu.x);
+    dd.y = fma(co, dd.y, uu.y);
+    acc = fma(ww.x, ww.x, acc);
+    acc = fma(ww.y, ww.y, acc);
+    u2v[i] = u2;
+    wv[i] = ww;
+    dv[i] = dd;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {
+    const int64_t i = n - 1;
+    if (pend) a.x[i] = fma(ex, a.d[i], a.x[i]);
+    a.u2[i] = fma(-alpha, a.v[i], a.u[i]);
+    a.w[i] = fma(-alpha, a.p[i], a.w[i]);
+    a.d[i] = fma(co, a.d[i], a.u[i]);
+    acc = fma(a.w[i], a.w[i], acc);
+  }
+  double v[1] = {acc}, tot[1];
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    TqState* st = a.st;
+    st->ww = tot[0];
+    if (!HOST) {
+      if (!quasi_update(st, tot[0])) {
+        st->pending = 0;
+        st->iter += 1;  // the iteration stopped inside its first half-step
+        st->done = kDoneBreakdown;
+      } else {
+        st->co = st->theta * st->theta * st->eta / st->alpha;
+        if (st->tau == 0.0) {  // the quasi-residual vanished: x is exact after this half-step
+          st->iter += 1;
+          st->done = kDoneConverged;
+        }
+      }
+    }
+  }
+}
+
+// T2, the even half-step: q = M u2 and the updates, ||w||^2 and (w, r*); the
+// test and beta in the last block.
+template <bool HOST, bool LONG>
+__global__ void __launch_bounds__(kThreads) t2_kernel(TqArgs a, HostScalars h, cudaGraphConditionalHandle cond,
+                                                      int32_t use_cond) {
+  if (!HOST && read_done(a.st)) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+      a.st->body_runs += 1;
+      cudaGraphSetConditional(cond, 0u);
+    }
+    return;
+  }
+  const double alpha = HOST ? h.alpha : a.st->alpha;
+  const double co = HOST ? h.co : a.st->co;
+  const bool pend = HOST ? h.pending != 0 : a.st->pending != 0;
+  const double ex = HOST ? h.eta_x : a.st->eta_x;
+  __shared__ double red[2 * kThreads];
+  double v[2] = {0.0, 0.0};
+  dev::sell_spmv<true, LONG, double>(a.A, a.u2, [&](int32_t i, double au2, double u2i) {
+                                          const double qi = __ldg(a.dinv + i) * au2;
+                                          double di = a.d[i];
+                                          if (pend) a.x[i] = fma(ex, di, a.x[i]);
+                                          const double wi = fma(-alpha, qi, a.w[i]);
+                                          di = fma(co, di, u2i);
+                                          a.q[i] = qi;
+                                          a.w[i] = wi;
+                                          a.d[i] = di;
+                                          v[0] = fma(wi, wi, v[0]);
+                                          v[1] = fma(wi, __ldg(a.rs + i), v[1]);
+                                        });
+  double tot[2];
+  if (dev::grid_sum_last<2>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    TqState* st = a.st;
+    st->ww = tot[0];
+    st->wr = tot[1];
+    if (!HOST) {
+      const int32_t it = st->iter + 1;
+      st->iter = it;
+      int32_t done = 0;
+      if (!quasi_update(st, tot[0])) {
+        st->pending = 0;
+        done = kDoneBreakdown;
+      } else {
+        const bool check = (it % st->check_every == 0) || it >= st->max_it;
+        if (st->tau == 0.0 || (check && sqrt(2.0 * it + 1.0) * st->tau <= st->tol)) {
+          done = kDoneConverged;
+        } else if (it >= st->max_it) {
+          done = kDoneNotConverged;
+        } else if (st->rho == 0.0 || !isfinite(tot[1])) {
+          done = kDoneBreakdown;
+        } else {
+          const double beta = tot[1] / st->rho;
+          st->beta = beta;
+          st->rho = tot[1];
+          if (it - 1 < st->hist_len) a.beta_h[it - 1] = beta;
+        }
+      }
+      st->done = done;
+      if (use_cond) {
+        st->body_runs += 1;
+        cudaGraphSetConditional(cond, done ? 0u : 1u);
+      }
+    }
+  }
+}
+
+// T3, the direction update: u = w + beta u2;  p = M w + beta q (= M u);
+// v = p + beta (q + beta v);  sigma = (v, r*) and alpha in the last block.
+template <bool HOST, bool LONG>
+__global__ void __launch_bounds__(kThreads) t3_kernel(TqArgs a, HostScalars h) {
+  if (!HOST && read_done(a.st)) return;
+  const double beta = HOST ? h.beta : a.st->beta;
+  __shared__ double red[kThreads];
+  double v[1] = {0.0};
+  dev::sell_spmv<true, LONG, double>(a.A, a.w, [&](int32_t i, double aw, double wi) {
+                                          const double mwi = __ldg(a.dinv + i) * aw;
+                                          const double qi = a.q[i];
+                                          a.u[i] = fma(beta, a.u2[i], wi);
+                                          const double pi = fma(beta, qi, mwi);
+                                          const double ti = fma(beta, a.v[i], qi);
+                                          const double vi = fma(beta, ti, pi);
+                                          a.p[i] = pi;
+                                          a.v[i] = vi;
+                                          v[0] = fma(vi, __ldg(a.rs + i), v[0]);
+                                        });
+  double tot[1];
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+    TqState* st = a.st;
+    st->sigma = tot[0];
+    if (!HOST) {
+      if (tot[0] == 0.0 || !isfinite(tot[0])) {
+        st->done = kDoneBreakdown;
+      } else {
+        const double alpha = st->rho / tot[0];
+        st->alpha = alpha;
+        st->co = st->theta * st->theta * st->eta / alpha;
+        if (st->iter < st->hist_len) a.alpha_h[st->iter] = alpha;
+      }
+    }
+  }
+}
+
+// The update still pending when the iteration stops: x += eta_x d.
+__global__ void __launch_bounds__(kThreads) finish_kernel(TqArgs a, HostScalars h, int32_t host) {
+  const bool pend = host ? h.pending != 0 : a.st->pending != 0;
+  if (!pend) return;
+  const double ex = host ? h.eta_x : a.st->eta_x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    a.x[i] = fma(ex, a.d[i], a.x[i]);
+}
+
+template <class K>
+int occupancy_grid(K kernel, int sms, int64_t want) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int64_t g = (int64_t)per_sm * sms;
+  if (want < g) g = want;
+  if (g > dev::kMaxPartials) g = dev::kMaxPartials;
+  return g < 1 ? 1 : (int)g;
+}
+
+// The host's copy of the quasi-residual update (host-synchronous form); the
+// same operations in the same order as quasi_update.
+bool host_quasi_update(TqState* h, double ww) {
+  const double theta = std::sqrt(ww) / h->tau;
+  const double c = 1.0 / std::sqrt(1.0 + theta * theta);
+  h->tau = h->tau * theta * c;
+  h->theta = theta;
+  h->eta = c * c * h->alpha;
+  h->eta_x = h->eta;
+  h->pending = 1;
+  return std::isfinite(theta) && std::isfinite(h->tau);
+}
+
+}  // namespace tq
+}  // namespace apcg
+
+struct apcg_tfqmr_plan_s {
+  apcg_ctx ctx = nullptr;
+  apcg_mat_s A;  // copy of the (non-owning) matrix view
+  apcg_cg_opts opts{};
+  int32_t mode = APCG_MODE_ASYNC_GRAPH;
+  apcg::tq::TqArgs a{};  // x is filled in per solve
+  int32_t n = 0, k = 1, max_it = 0, hist_len = 0;
+  int grid_spmv = 1, grid_vec = 1;
+  bool long_rows = false;
+  char* ws = nullptr;
+  apcg::tq::TqState* st_host = nullptr;  // pinned mirror of the state block
+  apcg_id id = 0;
+  bool pending = false;
+  int64_t last_launches = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double* graph_x = nullptr;
+};
+
+namespace apcg {
+namespace tq {
+
+using Plan = apcg_tfqmr_plan;
+
+TqArgs args_for(Plan P, double* x) {
+  TqArgs a = P->a;
+  a.x = x;
+  return a;
+}
+
+apcg_status launch_s1(Plan P, double* x, const double* b, cudaStream_t s) {
+  const TqArgs a = args_for(P, x);
+  const double rtol = P->opts.rtol, atol = P->opts.atol;
+  if (P->long_rows)
+    s1_kernel<true><<<P->grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, P->max_it, P->k, P->hist_len);
+  else
+    s1_kernel<false><<<P->grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, P->max_it, P->k, P->hist_len);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+apcg_status launch_s2(Plan P, double* x, cudaStream_t s, bool host) {
+  const TqArgs a = args_for(P, x);
+  if (host)
+    P->long_rows ? s2_kernel<true, true><<<P->grid_spmv, kThreads, 0, s>>>(a)
+                 : s2_kernel<true, false><<<P->grid_spmv, kThreads, 0, s>>>(a);
+  else
+    P->long_rows ? s2_kernel<false, true><<<P->grid_spmv, kThreads, 0, s>>>(a)
+                 : s2_kernel<false, false><<<P->grid_spmv, kThreads, 0, s>>>(a);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+apcg_status launch_t1(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h) {
+  const TqArgs a = args_for(P, x);
+  if (host)
+    t1_kernel<true><<<P->grid_vec, kThreads, 0, s>>>(a, h);
+  else
+    t1_kernel<false><<<P->grid_vec, kThreads, 0, s>>>(a, h);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+apcg_status launch_t2(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h,
+                      cudaGraphConditionalHandle cond, int32_t use_cond) {
+  const TqArgs a = args_for(P, x);
+  if (host)
+    P->long_rows ? t2_kernel<true, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond)
+                 : t2_kernel<true, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond);
+  else
+    P->long_rows ? t2_kernel<false, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond)
+                 : t2_kernel<false, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+apcg_status launch_t3(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h) {
+  const TqArgs a = args_for(P, x);
+  if (host)
+    P->long_rows ? t3_kernel<true, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h)
+                 : t3_kernel<true, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h);
+  else
+    P->long_rows ? t3_kernel<false, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h)
+                 : t3_kernel<false, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+apcg_status launch_finish(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h) {
+  finish_kernel<<<P->grid_vec, kThreads, 0, s>>>(args_for(P, x), h, host ? 1 : 0);
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+apcg_status read_state(Plan P, cudaStream_t s) {
+  APCG_CUDA(cudaMemcpyAsync(P->st_host, P->a.st, sizeof(TqState), cudaMemcpyDeviceToHost, s));
+  APCG_CUDA(cudaStreamSynchronize(s));
+  counters().d2h_copies++;
+  counters().d2h_bytes += sizeof(TqState);
+  counters().host_syncs++;
+  return APCG_OK;
+}
+
+// Host-synchronous form: each of the three reductions of an iteration goes to
+// the host and is waited for; alpha, beta and the half-step coefficients are
+// computed on the host and passed by value.
+apcg_status solve_host_sync(Plan P, const double* b, double* x) {
+  cudaStream_t s = P->ctx->stream;
+  TqState* h = P->st_host;
+  int64_t launches = 0;
+  APCG_TRY(launch_s1(P, x, b, s));
+  launches++;
+  APCG_TRY(read_state(P, s));
+  TqState m = *h;  // the host's scalars
+  std::vector<double> ah, bh;
+  HostScalars hs{};
+  auto scal = [&]() {
+    hs.alpha = m.alpha;
+    hs.beta = m.beta;
+    hs.co = m.co;
+    hs.eta_x = m.eta_x;
+    hs.pending = m.pending;
+    return hs;
+  };
+  int32_t done = m.done, it = 0;
+  if (!done) {
+    APCG_TRY(launch_s2(P, x, s, true));
+    launches++;
+    APCG_TRY(read_state(P, s));
+    if (h->sigma == 0.0 || !std::isfinite(h->sigma)) {
+      done = kDoneBreakdown;
+    } else {
+      m.alpha = m.rho / h->sigma;
+      m.co = 0.0;
+      ah.push_back(m.alpha);
+    }
+  }
+  while (!done) {
+    ++it;
+    APCG_TRY(launch_t1(P, x, s, true, scal()));
+    launches++;
+    APCG_TRY(read_state(P, s));
+    if (!host_quasi_update(&m, h->ww)) {
+      m.pending = 0;
+      done = kDoneBreakdown;
+      break;
+    }
+    m.co = m.theta * m.theta * m.eta / m.alpha;
+    if (m.tau == 0.0) {
+      done = kDoneConverged;
+      break;
+    }
+    APCG_TRY(launch_t2(P, x, s, true, scal(), 0, 0));
+    launches++;
+    APCG_TRY(read_state(P, s));
+    const double wr = h->wr;
+    if (!host_quasi_update(&m, h->ww)) {
+      m.pending = 0;
+      done = kDoneBreakdown;
+      break;
+    }
+    const bool check = (it % P->k == 0) || it >= P->max_it;
+    if (m.tau == 0.0 || (check && std::sqrt(2.0 * it + 1.0) * m.tau <= m.tol)) {
+      done = kDoneConverged;
+      break;
+    }
+    if (it >= P->max_it) {
+      done = kDoneNotConverged;
+      break;
+    }
+    if (m.rho == 0.0 || !std::isfinite(wr)) {
+      done = kDoneBreakdown;
+      break;
+    }
+    m.beta = wr / m.rho;
+    m.rho = wr;
+    if (it - 1 < P->hist_len) bh.push_back(m.beta);
+    APCG_TRY(launch_t3(P, x, s, true, scal()));
+    launches++;
+    APCG_TRY(read_state(P, s));
+    const double sigma = h->sigma;
+    if (sigma == 0.0 || !std::isfinite(sigma)) {
+      done = kDoneBreakdown;
+      break;
+    }
+    m.alpha = m.rho / sigma;
+    m.co = m.theta * m.theta * m.eta / m.alpha;
+    if (it < P->hist_len) ah.push_back(m.alpha);
+  }
+  APCG_TRY(launch_finish(P, x, s, true, scal()));
+  launches++;
+  APCG_CUDA(cudaStreamSynchronize(s));
+  counters().host_syncs++;
+  m.iter = it;
+  m.done = done;
+  *h = m;
+  P->last_launches = launches;
+  count_kernels(launches);
+  if (P->opts.alpha_hist)
+    for (size_t i = 0; i < ah.size() && (int)i < P->hist_len; ++i) P->opts.alpha_hist[i] = ah[i];
+  if (P->opts.beta_hist)
+    for (size_t i = 0; i < bh.size() && (int)i < P->hist_len; ++i) P->opts.beta_hist[i] = bh[i];
+  return APCG_OK;
+}
+
+void release_graph(Plan P) {
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  P->exec = nullptr;
+  P->graph = nullptr;
+  P->graph_x = nullptr;
+}
+
+// k iterations (T1, T2, T3 each) in the body of a conditional while node; the
+// last T2 of the body decides whether the body runs again.
+apcg_status build_graph(Plan P, double* x) {
+  if (P->exec && P->graph_x == x) return APCG_OK;
+  release_graph(P);
+  if (!P->cap_stream) APCG_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  APCG_CUDA(cudaGraphCreate(&g, 0));
+  P->graph = g;
+  cudaGraphConditionalHandle hnd;
+  APCG_CUDA(cudaGraphConditionalHandleCreate(&hnd, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  APCG_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  APCG_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const HostScalars none{};
+  apcg_status st = APCG_OK;
+  for (int j = 0; j < P->k && st == APCG_OK; ++j) {
+    st = launch_t1(P, x, P->cap_stream, false, none);
+    if (st == APCG_OK) st = launch_t2(P, x, P->cap_stream, false, none, hnd, j == P->k - 1 ? 1 : 0);
+    if (st == APCG_OK) st = launch_t3(P, x, P->cap_stream, false, none);
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(P->cap_stream, &captured);
+  if (st != APCG_OK) return st;
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  APCG_CUDA(cudaGraphInstantiate(&P->exec, g, 0));
+  APCG_CUDA(cudaGraphUpload(P->exec, P->ctx->stream));
+  P->graph_x = x;
+  return APCG_OK;
+}
+
+apcg_status enqueue_async(Plan P, const double* b, double* x, bool graph) {
+  cudaStream_t s = P->ctx->stream;
+  const HostScalars none{};
+  APCG_TRY(launch_s1(P, x, b, s));
+  APCG_TRY(launch_s2(P, x, s, false));
+  int64_t launches = 2;
+  if (graph) {
+    APCG_CUDA(cudaGraphLaunch(P->exec, s));
+    counters().graph_launches++;
+  } else {
+    // k iterations at a time, then one read of the state (the done word)
+    const int64_t max_blocks = (int64_t)P->max_it / P->k + 2;
+    for (int64_t blk = 0; blk < max_blocks; ++blk) {
+      for (int j = 0; j < P->k; ++j) {
+        APCG_TRY(launch_t1(P, x, s, false, none));
+        APCG_TRY(launch_t2(P, x, s, false, none, 0, 0));
+        APCG_TRY(launch_t3(P, x, s, false, none));
+      }
+      launches += 3 * P->k;
+      APCG_TRY(read_state(P, s));
+      if (P->st_host->done) break;
+    }
+  }
+  APCG_TRY(launch_finish(P, x, s, false, none));
+  launches++;
+  count_kernels(launches);
+  P->last_launches = launches;
+  APCG_CUDA(cudaMemcpyAsync(P->st_host, P->a.st, sizeof(TqState), cudaMemcpyDeviceToHost, s));
+  counters().d2h_copies++;
+  counters().d2h_bytes += sizeof(TqState);
+  return APCG_OK;
+}
+
+apcg_status finish_async(Plan P) {
+  APCG_CUDA(cudaStreamSynchronize(P->ctx->stream));
+  counters().host_syncs++;
+  if (P->mode == APCG_MODE_ASYNC_GRAPH) {
+    const int64_t body = (int64_t)P->st_host->body_runs * 3 * P->k;
+    count_kernels(body);
+    P->last_launches += body;
+  }
+  if (P->hist_len > 0) {
+    if (P->opts.alpha_hist)
+      APCG_CUDA(cudaMemcpy(P->opts.alpha_hist, P->a.alpha_h, sizeof(double) * P->hist_len, cudaMemcpyDeviceToHost));
+    if (P->opts.beta_hist)
+      APCG_CUDA(cudaMemcpy(P->opts.beta_hist, P->a.beta_h, sizeof(double) * P->hist_len, cudaMemcpyDeviceToHost));
+    counters().d2h_copies += 2;
+  }
+  return APCG_OK;
+}
+
+void fill_result(Plan P, apcg_cg_result* res) {
+  const TqState* h = P->st_host;
+  res->iters = h->iter;
+  res->reason = h->done == kDoneConverged ? APCG_CONVERGED
+                : h->done == kDoneBreakdown ? APCG_BREAKDOWN
+                                            : APCG_NOT_CONVERGED;
+  const double bound = std::sqrt(2.0 * h->iter + 1.0) * h->tau;
+  res->rr = bound * bound;
+  res->bnorm = std::sqrt(h->bnorm2);
+  res->rel_res = res->bnorm > 0.0 ? bound / res->bnorm : bound;
+  res->kernel_launches = P->last_launches;
+}
+
+apcg_status plan_destroy(Plan P) {
+  APCG_CHECK(P, "plan is NULL");
+  release_graph(P);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  if (P->ws) {
+    {
+      std::lock_guard<std::mutex> g(global_mutex());
+      reg_forget_memory(P->ws);
+    }
+    cudaFreeAsync(P->ws, P->ctx->stream);
+  }
+  if (P->st_host) {
+    cudaStreamSynchronize(P->ctx->stream);  // the pinned mirror may be the target of an enqueued copy
+    cudaFreeHost(P->st_host);
+  }
+  delete P;
+  return APCG_OK;
+}
+
+apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan* out) {
+  apcg_cg_opts o;
+  if (opts)
+    o = *opts;
+  else
+    apcg_cg_opts_default(&o);
+  APCG_CHECK(o.check_every >= 1, "check_every must be >= 1");
+  APCG_CHECK(o.rtol >= 0.0 && o.atol >= 0.0, "negative tolerance");
+  APCG_CHECK(o.history_len >= 0, "negative history length");
+  std::unique_ptr<apcg_tfqmr_plan_s, apcg_status (*)(Plan)> P(new apcg_tfqmr_plan_s(), plan_destroy);
+  P->ctx = ctx;
+  P->A = *A;
+  P->opts = o;
+  P->n = A->nrows;
+  P->k = o.check_every;
+  P->max_it = o.max_it > 0 ? o.max_it : (P->n > 0 ? 10 * P->n : 10);
+  P->hist_len = o.history_len;
+  P->mode = (o.mode == APCG_MODE_HOST_SYNC || o.mode == APCG_MODE_ASYNC) ? o.mode : APCG_MODE_ASYNC_GRAPH;
+  SellLayout L;
+  APCG_TRY(sell_layout(ctx->stream, P->n, A->rowptr, &L));
+  const int sms = ctx_num_sms(ctx);
+  P->long_rows = L.long_rows != 0;
+  const int64_t slices = ((int64_t)P->n + 31) / 32;
+  P->grid_spmv = P->long_rows ? occupancy_grid(t2_kernel<false, true>, sms, (slices + 7) / 8)
+                              : occupancy_grid(t2_kernel<false, false>, sms, (slices + 7) / 8);
+  P->grid_vec = occupancy_grid(t1_kernel<false>, sms, ((int64_t)P->n / 2 + kThreads - 1) / kThreads);
+  // Workspace: dinv, r*, u, u2, w, d, v, p, q; partials; state; histories; sliced-ELL copy.
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nv = up(sizeof(double) * (size_t)(P->n > 0 ? P->n : 1));
+  const size_t npart = up(sizeof(double) * dev::kMaxPartials * 2);
+  const size_t nst = up(sizeof(TqState));
+  const size_t nh = up(sizeof(double) * (size_t)(P->hist_len > 0 ? P->hist_len : 1));
+  const size_t nsptr = up(sizeof(int32_t) * ((size_t)L.nslices + 1));
+  const size_t ncol = up(sizeof(int32_t) * (size_t)std::max<int64_t>(L.padded, 1));
+  const size_t nval = up(sizeof(double) * (size_t)std::max<int64_t>(L.padded, 1));
+  const size_t total = 9 * nv + npart + nst + 2 * nh + nsptr + ncol + nval;
+  char* ws = nullptr;
+  APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
+  P->ws = ws;
+  double* vecs[9];
+  for (int i = 0; i < 9; ++i) vecs[i] = reinterpret_cast<double*>(ws + i * nv);
+  TqArgs& a = P->a;
+  a.n = P->n;
+  a.dinv = vecs[0];
+  a.rs = vecs[1];
+  a.u = vecs[2];
+  a.u2 = vecs[3];
+  a.w = vecs[4];
+  a.d = vecs[5];
+  a.v = vecs[6];
+  a.p = vecs[7];
+  a.q = vecs[8];
+  char* q = ws + 9 * nv;
+  a.partials = reinterpret_cast<double*>(q);
+  a.st = reinterpret_cast<TqState*>(q + npart);
+  a.alpha_h = reinterpret_cast<double*>(q + npart + nst);
+  a.beta_h = reinterpret_cast<double*>(q + npart + nst + nh);
+  APCG_CUDA(cudaMemsetAsync(q, 0, npart + nst + 2 * nh, ctx->stream));
+  q += npart + nst + 2 * nh;
+  int32_t* sptr = reinterpret_cast<int32_t*>(q);
+  int32_t* scol = reinterpret_cast<int32_t*>(q + nsptr);
+  double* sval = reinterpret_cast<double*>(q + nsptr + ncol);
+  APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice, ctx->stream));
+  counters().h2d_copies++;
+  APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val), scol,
+                                     sval));
+  a.A.n = P->n;
+  a.A.nslices = L.nslices;
+  a.A.sptr = sptr;
+  a.A.col = scol;
+  a.A.val = sval;
+  a.A.long_rows = L.long_rows;
+  APCG_CUDA(cudaMallocHost((void**)&P->st_host, sizeof(TqState)));
+  {
+    std::lock_guard<std::mutex> g(global_mutex());
+    P->id = register_memory(ws, total);
+  }
+  // A0: the Jacobi diagonal, checked once here.
+  OpScope op(ctx);
+  op.read(A->id).write(P->id);
+  APCG_TRY(op.begin());
+  if (P->n > 0) APCG_TRY(launch_jacobi_setup(ctx, A, vecs[0]));
+  APCG_TRY(op.finish());
+  APCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  counters().host_syncs++;
+  APCG_TRY(ctx_check_device_error(ctx));
+  *out = P.release();
+  return APCG_OK;
+}
+
+apcg_status check_solve_args(Plan P, apcg_vec b, apcg_vec x) {
+  APCG_CHECK(P, "plan is NULL");
+  APCG_CHECK(b && x, "b or x is NULL");
+  APCG_CHECK(b->dtype == APCG_F64 && x->dtype == APCG_F64, "b and x must be float64");
+  APCG_CHECK(b->n == P->n && x->n == P->n, "b/x length differs from the matrix size %d", P->n);
+  APCG_CHECK(P->n == 0 || (aligned16(b->dptr) && aligned16(x->dptr)), "b/x must be 16-byte aligned");
+  APCG_CHECK(b->dptr != x->dptr || P->n == 0, "b and x must not alias");
+  return APCG_OK;
+}
+
+}  // namespace tq
+}  // namespace apcg
+
+using namespace apcg;
+
+extern "C" {
+
+apcg_status apcg_tfqmr_plan_create(apcg_ctx ctx_in, apcg_mat A, const apcg_cg_opts* opts, apcg_tfqmr_plan* out) {
+  APCG_CHECK(A && out, "NULL argument");
+  APCG_CHECK(A->dtype == APCG_F64 && A->nrows == A->ncols, "TFQMR takes a square float64 matrix");
+  apcg_ctx ctx;
+  APCG_TRY(resolve_ctx(ctx_in, &ctx));
+  return tq::plan_create(ctx, A, opts, out);
+}
+
+apcg_status apcg_tfqmr_plan_solve(apcg_tfqmr_plan P, apcg_vec b, apcg_vec x, apcg_cg_result* res) {
+  APCG_CHECK(res, "res is NULL");
+  APCG_TRY(tq::check_solve_args(P, b, x));
+  double* xp = static_cast<double*>(x->dptr);
+  const double* bp = static_cast<const double*>(b->dptr);
+  if (P->mode == APCG_MODE_ASYNC_GRAPH) APCG_TRY(tq::build_graph(P, xp));
+  OpScope op(P->ctx);
+  op.read(P->A.id).read(b->id).rw(x->id).rw(P->id);
+  APCG_TRY(op.begin());
+  apcg_status st = P->mode == APCG_MODE_HOST_SYNC ? tq::solve_host_sync(P, bp, xp)
+                                                  : tq::enqueue_async(P, bp, xp, P->mode == APCG_MODE_ASYNC_GRAPH);
+  apcg_status st2 = op.finish();
+  APCG_TRY(st);
+  APCG_TRY(st2);
+  if (P->mode != APCG_MODE_HOST_SYNC) APCG_TRY(tq::finish_async(P));
+  tq::fill_result(P, res);
+  return APCG_OK;
+}
+
+apcg_status apcg_tfqmr_plan_destroy(apcg_tfqmr_plan P) { return tq::plan_destroy(P); }
+
+apcg_status apcg_tfqmr_solve(apcg_ctx ctx, apcg_mat A, apcg_vec b, apcg_vec x, const apcg_cg_opts* opts,
+                             apcg_cg_result* res) {
+  APCG_CHECK(res, "res is NULL");
+  apcg_tfqmr_plan P = nullptr;
+  APCG_TRY(apcg_tfqmr_plan_create(ctx, A, opts, &P));
+  apcg_status st = apcg_tfqmr_plan_solve(P, b, x, res);
+  tq::plan_destroy(P);
+  return st;
+}
+
+}  // extern "C"

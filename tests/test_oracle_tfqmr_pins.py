@@ -129,3 +129,20 @@ def test_tfqmr_pins_catch_planted_mistakes(mutation):
             if np.linalg.norm(bh - Mh @ r["x"]) > r["bound"] * (1 + 1e-10):
                 caught = True
     assert caught, mutation
+
+
+def test_tfqmr_rounding_sensitivity():
+    """One-ulp perturbations of b move TFQMR's alpha/beta far more on a nonsymmetric system than on a
+    symmetric one, where both TFQMR's and CG's stay at rounding level (the reason the GPU parity bar for
+    TFQMR is scaled by the measured sensitivity)."""
+
+    def sens(solver, A, b):
+        ref = solver(A, b, rtol=1e-8, hist_len=10)
+        sign = np.random.default_rng(3).choice([-1.0, 1.0], b.size)
+        o = solver(A, b * (1.0 + sign * 2.0**-53), rtol=1e-8, hist_len=10)
+        return max(float(np.max(np.abs(o[k] - ref[k]) / np.abs(ref[k]))) for k in ("alpha", "beta"))
+
+    (A1, b1), (A2, b2) = _problems()
+    assert sens(oracle.tfqmr, A1, b1) <= 1e-13
+    assert sens(oracle.pcg, A1, b1) <= 1e-13
+    assert sens(oracle.tfqmr, A2, b2) >= 1e-14
