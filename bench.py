@@ -290,6 +290,13 @@ def run_apcg(args, rank, world, local):
             "traffic": trec["traffic_bytes_per_launch"] if trec else None,
             "algorithmic_bytes": bytes_k1,
             "avg_launch_ms": ms_k[0],
+            # the second bound of this kernel on GB300: one float64 FMA per stored entry and per row for (p,w)
+            "fp64": {
+                "achieved_gflops": 2.0 * (nnz + n) / (ms_k[0] * 1e-3) / 1e9,
+                "peak_gflops": 1257.0,
+                "peak_kind": "nominal: 2 float64 FMA lanes per SM per cycle x 152 SMs x 2.07 GHz",
+                "frac": 2.0 * (nnz + n) / (ms_k[0] * 1e-3) / 1e9 / 1257.0,
+            },
         }
         us_iter = 1e3 * ms_step / it
         out["iteration"] = {
