@@ -1,4 +1,4 @@
-"""CPU oracle for the Jacobi-preconditioned CG and TFQMR paths (test infrastructure).
+"""CPU oracle for the Jacobi-preconditioned CG and TFQMR paths and the stencil operator (test infrastructure).
 
 Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 leg may import this package.  The product path never does; it shares no code
@@ -14,6 +14,7 @@ from .oracle import (  # noqa: F401
     diagonal,
     pcg,
     tfqmr,
+    stencil_apply,
     pcg_f32,
     ir,
 )

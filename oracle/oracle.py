@@ -1,4 +1,4 @@
-"""ctypes front end of the plain C oracle (``pcg_oracle.c``, ``tfqmr_oracle.c``).
+"""ctypes front end of the plain C oracle (``pcg_oracle.c``, ``tfqmr_oracle.c``, ``stencil_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: only the tests, the smoke check and the benchmark's
 CPU-baseline leg may use it.  The library is compiled with gcc (ISO C11,
@@ -20,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "pcg_oracle.c"), os.path.join(_HERE, "tfqmr_oracle.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("pcg_oracle.c", "tfqmr_oracle.c", "stencil_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -90,6 +90,8 @@ def load():
             lib.oracle_ir.restype = C.c_int
             lib.oracle_tfqmr.argtypes = [i64, P, P, P, P, P, f64, f64, i32, i32, i32, P, P, P, i32, C.POINTER(_TqRes)]
             lib.oracle_tfqmr.restype = C.c_int
+            lib.oracle_stencil_apply.argtypes = [i32, i32, i32, i32, P, P, P, P, i32]
+            lib.oracle_stencil_apply.restype = None
             _lib = lib
     return _lib
 
@@ -182,6 +184,18 @@ def tfqmr(A, b, x0=None, rtol=1e-8, atol=0.0, max_it=None, check_every=1, hist_l
     for k, v in hs.items():
         out[k] = v[:H]
     return out
+
+
+def stencil_apply(dims, offsets, weights, x, mutation=0) -> np.ndarray:
+    """y = S x for a constant-coefficient stencil on an nx x ny x nz grid (Dirichlet: outside terms dropped)."""
+    nx, ny, nz = (int(v) for v in dims)
+    offs = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    assert offs.shape[0] == w.shape[0]
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(nx * ny * nz, dtype=np.float64)
+    load().oracle_stencil_apply(nx, ny, nz, offs.shape[0], _p(offs), _p(w), _p(x), _p(y), int(mutation))
+    return y
 
 
 def pcg_f32(A, bf, rtol=1e-4, max_it=1000, check_every=1, x0=None) -> dict:

@@ -22,6 +22,8 @@ from .stencils import (  # noqa: F401
     random_spd_csr,
     graph_laplacian_csr,
     convection_diffusion_2d,
+    stencil_terms,
+    stencil_matrix,
     sine_mode_2d,
     sine_mode_3d,
     rhs_from_solution,

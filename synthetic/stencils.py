@@ -109,6 +109,29 @@ def _neighbours(ndim, full):
     return out
 
 
+STENCIL_KINDS = {"5pt": (2, False, 4.0), "9pt": (2, True, 8.0), "7pt": (3, False, 6.0), "27pt": (3, True, 26.0)}
+
+
+def stencil_terms(kind: str, dims, shift: float = 0.0):
+    """Terms (offsets [k, 3], weights [k]) of the constant Laplace stencils above, in ascending order of
+    the linear offset dx + nx (dy + ny dz) -- the column order of the assembled rows.
+
+    kind: "5pt" and "9pt" (2-D, nz = 1), "7pt" and "27pt" (3-D); all neighbours -1, centre the number of
+    neighbours (+ shift)."""
+    ndim, full, diag = STENCIL_KINDS[kind]
+    nx, ny, _ = dims
+    offs = _neighbours(ndim, full) + [(0, 0, 0)]
+    offs.sort(key=lambda o: o[0] + nx * (o[1] + ny * o[2]))
+    w = [diag + shift if o == (0, 0, 0) else -1.0 for o in offs]
+    return np.array(offs, dtype=np.int32), np.array(w, dtype=np.float64)
+
+
+def stencil_matrix(kind: str, dims, shift: float = 0.0) -> CSR:
+    """The assembled CSR of stencil_terms(kind, dims, shift) on a grid of the given dims."""
+    ndim, full, diag = STENCIL_KINDS[kind]
+    return _assemble(tuple(int(d) for d in dims), _neighbours(ndim, full), lambda k, v, j: -1.0, diag + shift)
+
+
 def laplace_2d_5pt(N: int, shift: float = 0.0) -> CSR:
     """5-point Laplacian on an N x N grid: diagonal 4 (+shift), neighbours -1."""
     offs = _neighbours(2, full=False)
