@@ -441,8 +441,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="only the set-up and 3 iterations, kernels launched one by one (for profilers)")
-    ap.add_argument("--config", choices=["c2", "c3", "c4", "c5", "tfqmr"], default="c2",
-                    help="c2: the headline 128^3 workload (default); c3/c4/c5/tfqmr: extra measurement lines")
+    ap.add_argument("--config", choices=["c2", "c3", "c4", "c5", "tfqmr", "stencil"], default="c2",
+                    help="c2: the headline 128^3 workload (default); c3/c4/c5/tfqmr/stencil: extra measurement lines")
     ap.add_argument("--no-tune", action="store_true", help="c4/c5: skip the batched autotuner")
     args = ap.parse_args()
     rank, world, local = _env_rank()
@@ -464,7 +464,7 @@ def main():
         ncu_case()
         return
     if args.config != "c2":
-        {"c3": bench_c3, "c4": bench_c4, "c5": bench_c5, "tfqmr": bench_tfqmr}[args.config](args)
+        {"c3": bench_c3, "c4": bench_c4, "c5": bench_c5, "tfqmr": bench_tfqmr, "stencil": bench_stencil}[args.config](args)
         return
     run_apcg(args, rank, world, local)
 
@@ -701,6 +701,85 @@ def bench_c5(args):
     out["max_rel_err_vs_fp64_batched"] = float(err_64)
     line = {"metric": "batched mixed-precision solves/s at rtol 1e-10", "value": B.nsys / dt_ir, "unit": "solves/s",
             "dtype": "f32+f64", "data": "synthetic", **out}
+    print(json.dumps(line), flush=True)
+
+
+def bench_stencil(args):
+    """Jacobi-PCG at rtol 1e-8 on 128^3 7-point and 27-point Laplacians: the matrix-free stencil operator
+    against the sliced-ELL CSR path, same right-hand side, graph mode, k = 10."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+    from synthetic import rhs_from_solution, stencil_matrix, stencil_terms
+
+    V = C.c_void_p
+    dev = torch.device("cuda", 0)
+    apcg.load()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = apcg.ctx_create(stream)
+    N = 128
+    dims = (N, N, N)
+    out = {"config": {"workload": "Jacobi-PCG to rtol 1e-8 (k=10, graph mode) on 128^3 7-point and 27-point Laplacians: "
+                                  "matrix-free stencil vs CSR"}}
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+
+    def timed(plan, vb, vx, x):
+        best, r = None, None
+        for i in range(max(2, args.steps // 3) + 1):
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = apcg.cg_plan_solve(plan, vb, vx)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+        return best, r
+
+    for kind in ("7pt", "27pt"):
+        A = stencil_matrix(kind, dims)
+        b = rhs_from_solution(A, np.random.default_rng(0).uniform(-1, 1, A.n))
+        bt = t(b)
+        x = torch.zeros_like(bt)
+        vb, vx = apcg.vec_wrap(bt), apcg.vec_wrap(x)
+        opts = apcg.cg_opts(rtol=1e-8, check_every=10, mode="async_graph", max_it=5000)
+        row = {"n": A.n, "nnz": A.nnz}
+        offs, w = stencil_terms(kind, dims)
+        S = apcg.stencil_create(dims, offs, w)
+        plan = apcg.cg_plan_create_stencil(ctx, S, opts)
+        apcg.call("apcg_stencil_destroy", V(S))
+        ms, r = timed(plan, vb, vx, x)
+        k_ms = apcg.cg_plan_profile(plan, vb, vx, 20)
+        apcg.call("apcg_cg_plan_destroy", V(plan))
+        assert r["reason"] == "converged"
+        row["stencil"] = {"ms_per_solve": ms, "iters": r["iters"], "us_per_iteration": 1e3 * ms / r["iters"],
+                          "kernel_us": [1e3 * v for v in k_ms], "bytes_per_iteration": 120 * A.n,
+                          "GBps_per_iteration": 120 * A.n / (1e-3 * ms / r["iters"]) / 1e9}
+        rowptr, col, val = t(A.rowptr), t(A.col), t(A.val)
+        M = apcg.mat_wrap(rowptr, col, val)
+        plan = apcg.cg_plan_create(ctx, M, opts)
+        ms2, r2 = timed(plan, vb, vx, x)
+        k2 = apcg.cg_plan_profile(plan, vb, vx, 20)
+        apcg.call("apcg_cg_plan_destroy", V(plan))
+        b_csr = 12 * A.nnz + 4 * (A.n + 1) + 104 * A.n
+        row["csr"] = {"ms_per_solve": ms2, "iters": r2["iters"], "us_per_iteration": 1e3 * ms2 / r2["iters"],
+                      "kernel_us": [1e3 * v for v in k2], "bytes_per_iteration": b_csr,
+                      "GBps_per_iteration": b_csr / (1e-3 * ms2 / r2["iters"]) / 1e9}
+        row["speedup_stencil_vs_csr"] = ms2 / ms
+        # the matrix-free K1 is bound by the float64 pipe: one FMA per term and one per row for (p,w)
+        fl = 2.0 * (len(w) + 1) * A.n
+        row["stencil"]["k1_fp64_gflops"] = fl / (k_ms[0] * 1e-3) / 1e9
+        row["stencil"]["k1_fp64_frac_of_nominal_1257"] = fl / (k_ms[0] * 1e-3) / 1e9 / 1257.0
+        out[kind] = row
+        for h, fn in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (M, "apcg_mat_destroy")):
+            apcg.call(fn, V(h))
+    line = {"metric": "matrix-free stencil PCG solves/s at rtol 1e-8 (FP64)", "value": 1e3 / out["7pt"]["stencil"]["ms_per_solve"],
+            "unit": "solves/s", "dtype": "f64", "data": "synthetic", **out}
     print(json.dumps(line), flush=True)
 
 

@@ -473,6 +473,42 @@ APCG_API apcg_status apcg_ir_plan_destroy(apcg_ir_plan plan);
 APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
                                    const apcg_ir_opts* opts, apcg_ir_result* res);
 
+/* ------------------------------------------------------------------ matrix-free stencil operators */
+
+/*
+ * A constant-coefficient stencil on an nx x ny x nz grid (x fastest, then y,
+ * then z; row i = ix + nx (iy + ny iz)), applied without a matrix: the
+ * finite-difference Laplace operators of Sec. 4.1, which the paper's JAX
+ * comparison applies as a convolution (Sec. 4.4).  Row i of S x is
+ *   sum over terms k of weights[k] * x[i + dx_k + nx (dy_k + ny dz_k)],
+ * where a term whose neighbour (ix + dx_k, iy + dy_k, iz + dz_k) lies outside
+ * the grid is dropped (Dirichlet boundary by elimination: S is the assembled
+ * stencil matrix).  The terms are summed in ascending order of their linear
+ * offset, the column order of an assembled row.
+ *
+ * offsets: host int32 [npts][3] = (dx, dy, dz), each within +-127, no offset
+ * twice; weights: host float64 [npts], finite; 1 <= npts <= 27; nx ny nz
+ * <= 2^31 - 1.  Both arrays are copied.  The object holds no device memory.
+ */
+typedef struct apcg_stencil_s* apcg_stencil;
+APCG_API apcg_status apcg_stencil_create(int32_t nx, int32_t ny, int32_t nz, int32_t npts, const int32_t* offsets,
+                                         const double* weights, apcg_stencil* out);
+APCG_API apcg_status apcg_stencil_destroy(apcg_stencil stencil);
+/* y = S x (device float64 [nx ny nz], not aliased).  Marks x read, y written. */
+APCG_API apcg_status apcg_stencil_apply_async(apcg_ctx ctx, apcg_stencil stencil, apcg_vec x, apcg_vec y);
+/*
+ * A Jacobi-PCG plan on a stencil operator: the method, modes, options and
+ * results of apcg_cg_plan_create, with the SpMV reading only x (no matrix
+ * arrays).  The Jacobi diagonal is 1 / (the weight of the (0,0,0) term);
+ * APCG_ERR_BAD_DIAGONAL if that term is missing, zero or not finite.  Modes:
+ * HOST_SYNC, ASYNC, ASYNC_GRAPH (AUTO selects ASYNC_GRAPH; PERSISTENT returns
+ * APCG_ERR_UNSUPPORTED: the whole-solve cluster kernel reads a CSR matrix).
+ * Solve, profile and destroy with the apcg_cg_plan_* calls above.  The plan
+ * copies the stencil; the stencil may be destroyed afterwards.
+ */
+APCG_API apcg_status apcg_cg_plan_create_stencil(apcg_ctx ctx, apcg_stencil stencil, const apcg_cg_opts* opts,
+                                                 apcg_cg_plan* out);
+
 /* ------------------------------------------------------------------ TFQMR */
 
 /*

@@ -215,6 +215,10 @@ PROTOS = {
     "apcg_ir_plan_solve": [P, P, P, C.POINTER(IrResult)],
     "apcg_ir_plan_destroy": [P],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
+    "apcg_stencil_create": [i32, i32, i32, i32, P, P, PP],
+    "apcg_stencil_destroy": [P],
+    "apcg_stencil_apply_async": [P, P, P, P],
+    "apcg_cg_plan_create_stencil": [P, P, C.POINTER(CgOpts), PP],
     "apcg_tfqmr_plan_create": [P, P, C.POINTER(CgOpts), PP],
     "apcg_tfqmr_plan_solve": [P, P, P, C.POINTER(CgResult)],
     "apcg_tfqmr_plan_destroy": [P],
@@ -456,6 +460,24 @@ def cg_solve_host(rowptr, col, val, b, x, opts: CgOpts) -> dict:
         C.byref(res),
     )
     return res.as_dict()
+
+
+def stencil_create(dims, offsets, weights):
+    """A stencil operator handle; dims = (nx, ny, nz), offsets [k][3] ints, weights [k] floats."""
+    import numpy as np
+
+    offs = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    h = _out()
+    nx, ny, nz = (int(d) for d in dims)
+    call("apcg_stencil_create", nx, ny, nz, offs.shape[0], offs.ctypes.data_as(P), w.ctypes.data_as(P), C.byref(h))
+    return h.value
+
+
+def cg_plan_create_stencil(ctx, stencil, opts: CgOpts):
+    h = _out()
+    call("apcg_cg_plan_create_stencil", C.c_void_p(ctx), C.c_void_p(stencil), C.byref(opts), C.byref(h))
+    return h.value
 
 
 def tfqmr_solve(ctx, A, b, x, opts: CgOpts) -> dict:

@@ -239,10 +239,19 @@ apcg_status cg_plan_destroy(apcg_cg_plan P) {
   return APCG_OK;
 }
 
-apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, apcg_cg_plan* out) {
-  APCG_CHECK(A && out, "NULL argument");
-  APCG_CHECK(A->dtype == APCG_F64, "the CG solver takes a float64 matrix");
-  APCG_CHECK(A->nrows == A->ncols, "the matrix must be square");
+// A plan on a CSR matrix (A) or on a stencil operator (S); exactly one is given.
+apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, const apcg_cg_opts* opts,
+                           apcg_cg_plan* out) {
+  APCG_CHECK((A || S) && !(A && S) && out, "NULL argument");
+  double center = 0.0;
+  if (A) {
+    APCG_CHECK(A->dtype == APCG_F64, "the CG solver takes a float64 matrix");
+    APCG_CHECK(A->nrows == A->ncols, "the matrix must be square");
+  } else {
+    center = stencil_center(S);
+    if (!(center != 0.0) || !std::isfinite(center))
+      return set_error(APCG_ERR_BAD_DIAGONAL, "Jacobi: the stencil's centre weight is missing, zero or not finite");
+  }
   apcg_cg_opts o;
   if (opts)
     o = *opts;
@@ -254,15 +263,25 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
   APCG_CHECK(o.mode >= APCG_MODE_HOST_SYNC && o.mode <= APCG_MODE_AUTO, "bad mode %d", o.mode);
   std::unique_ptr<apcg_cg_plan_s, apcg_status (*)(apcg_cg_plan)> P(new apcg_cg_plan_s(), cg_plan_destroy);
   P->ctx = ctx;
-  P->A = *A;
+  if (A) {
+    P->A = *A;
+  } else {
+    P->A = apcg_mat_s{};
+    P->A.nrows = P->A.ncols = stencil_view(S).n;
+    P->A.dtype = APCG_F64;
+  }
   P->opts = o;
   CgCore<double>& c = P->core;
-  c.n = A->nrows;
+  c.n = P->A.nrows;
+  if (S) c.S = stencil_view(S);
   c.k = o.check_every;
   c.max_it = o.max_it > 0 ? o.max_it : (c.n > 0 ? 10 * c.n : 10);
   c.hist_len = o.history_len;
   P->mode = o.mode;
-  if (o.mode == APCG_MODE_PERSISTENT || o.mode == APCG_MODE_AUTO) {
+  if (S && o.mode == APCG_MODE_PERSISTENT)
+    return set_error(APCG_ERR_UNSUPPORTED, "the whole-solve cluster kernel takes a CSR matrix, not a stencil");
+  if (S && o.mode == APCG_MODE_AUTO) P->mode = APCG_MODE_ASYNC_GRAPH;
+  if (A && (o.mode == APCG_MODE_PERSISTENT || o.mode == APCG_MODE_AUTO)) {
     P->shape = c.n <= kPersistentMaxRows ? default_cluster_shape(c.n) : ClusterShape{};
     if (c.n > kPersistentMaxRows) P->shape.ok = false;
     if (!P->shape.ok) {
@@ -274,10 +293,10 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
       P->mode = APCG_MODE_PERSISTENT;
     }
   }
-  core_configure(c, A->nnz, ctx_num_sms(ctx));
+  core_configure(c, A ? A->nnz : 0, ctx_num_sms(ctx));
   // The iteration kernels read a sliced-ELL copy of A (sell.cuh); the cluster kernel reads the CSR itself.
   SellLayout L;
-  const bool need_sell = P->mode != APCG_MODE_PERSISTENT;
+  const bool need_sell = A && P->mode != APCG_MODE_PERSISTENT;
   if (need_sell) APCG_TRY(sell_layout(ctx->stream, c.n, A->rowptr, &L));
   // Workspace: dinv, r, p, w, z, partials, state, histories, cluster bookkeeping (one stream-ordered block).
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -336,11 +355,13 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, a
     std::lock_guard<std::mutex> g(global_mutex());
     P->id = register_memory(ws, total);
   }
-  // A0: the Jacobi diagonal, checked once here.
+  // A0: the Jacobi diagonal, checked once here (a stencil's is the constant 1 / centre).
   OpScope op(ctx);
-  op.read(A->id).write(P->id);
+  if (A) op.read(A->id);
+  op.write(P->id);
   APCG_TRY(op.begin());
-  if (c.n > 0) APCG_TRY(launch_jacobi_setup(ctx, A, c.dinv));
+  if (c.n > 0 && A) APCG_TRY(launch_jacobi_setup(ctx, A, c.dinv));
+  if (c.n > 0 && S) APCG_TRY(launch_fill(ctx, c.dinv, c.n, 1.0 / center));
   APCG_TRY(op.finish());
   APCG_CUDA(cudaStreamSynchronize(ctx->stream));
   counters().host_syncs++;
@@ -411,7 +432,15 @@ apcg_status apcg_cg_plan_create(apcg_ctx ctx_in, apcg_mat A, const apcg_cg_opts*
   APCG_CHECK(A->dtype == APCG_F64 && A->nrows == A->ncols, "the CG solver takes a square float64 matrix");
   apcg_ctx ctx;
   APCG_TRY(resolve_ctx(ctx_in, &ctx));
-  return cg_plan_create(ctx, A, opts, out);
+  return cg_plan_create(ctx, A, nullptr, opts, out);
+}
+
+apcg_status apcg_cg_plan_create_stencil(apcg_ctx ctx_in, apcg_stencil S, const apcg_cg_opts* opts,
+                                        apcg_cg_plan* out) {
+  APCG_CHECK(S && out, "NULL argument");
+  apcg_ctx ctx;
+  APCG_TRY(resolve_ctx(ctx_in, &ctx));
+  return cg_plan_create(ctx, nullptr, S, opts, out);
 }
 
 apcg_status apcg_cg_plan_solve(apcg_cg_plan P, apcg_vec b, apcg_vec x, apcg_cg_result* res) {

@@ -34,6 +34,7 @@
 #include "cg_core.hpp"
 #include "kernels_common.cuh"
 #include "sell.cuh"
+#include "stencil.cuh"
 
 namespace apcg {
 namespace {
@@ -58,7 +59,8 @@ struct V16<float> {
 
 template <class T>
 struct Args {
-  dev::SellView<T> A;  // the plan's sliced-ELL copy of the matrix
+  dev::SellView<T> A;  // the plan's sliced-ELL copy of the matrix (CSR plans)
+  dev::StencilView S;  // the operator (stencil plans; S.n == 0 otherwise)
   int32_t n;
   const T* __restrict__ dinv;
   T* x;
@@ -76,6 +78,7 @@ template <class T>
 Args<T> make_args(const CgCore<T>& c, T* x) {
   Args<T> a;
   a.A = c.A;
+  a.S = c.S;
   a.n = c.n;
   a.dinv = c.dinv;
   a.x = x;
@@ -93,21 +96,22 @@ Args<T> make_args(const CgCore<T>& c, T* x) {
 __device__ __forceinline__ int32_t read_done(const CgState* st) { return *(volatile const int32_t*)&st->done; }
 
 // r = b - A x0, z = D^-1 r, p = z; rho = (r,z), rr = (r,r), bb = (b,b) (float64 solve).
-template <bool LONG>
-__global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const double* __restrict__ b, double rtol,
-                                                         double atol, int32_t max_it, int32_t k, int32_t hist_len) {
+// spmv(epi) applies the operator to x with the given row epilogue.
+template <class Spmv>
+__device__ __forceinline__ void setup_body(const Args<double>& a, const double* __restrict__ b, double rtol,
+                                           double atol, int32_t max_it, int32_t k, int32_t hist_len, Spmv spmv) {
   __shared__ double red[3 * kThreads];
   double v[3] = {0.0, 0.0, 0.0};
-  dev::sell_spmv<false, LONG, double>(a.A, a.x, [&](int32_t i, double ax, double) {
-                                           const double bi = __ldg(b + i);
-                                           const double ri = bi - ax;
-                                           const double zi = __ldg(a.dinv + i) * ri;
-                                           a.r[i] = ri;
-                                           a.p[i] = zi;
-                                           v[0] = fma(ri, zi, v[0]);
-                                           v[1] = fma(ri, ri, v[1]);
-                                           v[2] = fma(bi, bi, v[2]);
-                                         });
+  spmv([&](int32_t i, double ax, double) {
+    const double bi = __ldg(b + i);
+    const double ri = bi - ax;
+    const double zi = __ldg(a.dinv + i) * ri;
+    a.r[i] = ri;
+    a.p[i] = zi;
+    v[0] = fma(ri, zi, v[0]);
+    v[1] = fma(ri, ri, v[1]);
+    v[2] = fma(bi, bi, v[2]);
+  });
   double tot[3];
   if (dev::grid_sum_last<3>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
     CgState* st = a.st;
@@ -124,6 +128,21 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const d
     st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
     st->done = (sqrt(tot[1]) <= tol) ? kDoneConverged : 0;
   }
+}
+
+template <bool LONG>
+__global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const double* __restrict__ b, double rtol,
+                                                         double atol, int32_t max_it, int32_t k, int32_t hist_len) {
+  setup_body(a, b, rtol, atol, max_it, k, hist_len,
+             [&](auto epi) { dev::sell_spmv<false, LONG, double>(a.A, a.x, epi); });
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads) setup_stencil_kernel(Args<double> a, const double* __restrict__ b,
+                                                                 double rtol, double atol, int32_t max_it, int32_t k,
+                                                                 int32_t hist_len) {
+  setup_body(a, b, rtol, atol, max_it, k, hist_len,
+             [&](auto epi) { dev::stencil_spmv<NP, false, double>(a.S, a.x, epi); });
 }
 
 // The last block of K1: gamma, and alpha = rho / gamma (device mode) or a breakdown flag.
@@ -152,6 +171,20 @@ __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
                                      a.w[i] = s;
                                      v[0] = fma(p_i, s, v[0]);
                                    });
+  T tot[1];
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0]);
+}
+
+// K1 on a stencil operator (stencil.cuh): the same per-row arithmetic.
+template <bool HOST, int NP, class T>
+__global__ void __launch_bounds__(kThreads) k1_stencil_kernel(Args<T> a) {
+  if (!HOST && read_done(a.st)) return;
+  __shared__ T red[kThreads];
+  T v[1] = {T(0)};
+  dev::stencil_spmv<NP, true, T>(a.S, a.p, [&](int32_t i, T s, T p_i) {
+    a.w[i] = s;
+    v[0] = fma(p_i, s, v[0]);
+  });
   T tot[1];
   if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0]);
 }
@@ -334,7 +367,21 @@ int occupancy_grid(K kernel, int sms, int64_t want) {
 }
 
 template <bool HOST, class T>
+apcg_status k1_stencil_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
+  switch (c.S.npts) {
+    case 5: k1_stencil_kernel<HOST, 5, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+    case 7: k1_stencil_kernel<HOST, 7, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+    case 9: k1_stencil_kernel<HOST, 9, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+    case 27: k1_stencil_kernel<HOST, 27, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+    default: k1_stencil_kernel<HOST, 0, T><<<c.grid_spmv, kThreads, 0, s>>>(a); break;
+  }
+  APCG_CUDA(cudaGetLastError());
+  return APCG_OK;
+}
+
+template <bool HOST, class T>
 apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
+  if (c.S.n > 0) return k1_stencil_dispatch<HOST>(c, a, s);
   if (c.A.long_rows)
     k1_kernel<HOST, true, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
   else
@@ -351,8 +398,11 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
   const int64_t slices = ((int64_t)c.n + 31) / 32;
   const int64_t spmv_blocks = (slices + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t vec_blocks = (((int64_t)c.n / V16<T>::E) + (int64_t)kThreads * kUpdV - 1) / ((int64_t)kThreads * kUpdV);
-  c.grid_spmv = occupancy_grid(c.A.long_rows ? (void*)k1_kernel<false, true, T> : (void*)k1_kernel<false, false, T>, sms,
-                               spmv_blocks);
+  if (c.S.n > 0)
+    c.grid_spmv = occupancy_grid((void*)k1_stencil_kernel<false, 7, T>, sms, ((int64_t)c.n + kThreads - 1) / kThreads);
+  else
+    c.grid_spmv = occupancy_grid(c.A.long_rows ? (void*)k1_kernel<false, true, T> : (void*)k1_kernel<false, false, T>,
+                                 sms, spmv_blocks);
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
 }
 
@@ -432,7 +482,16 @@ apcg_status core_build_graph(CgCore<T>& c, T* x, cudaStream_t upload) {
 apcg_status core_setup_f64(const CgCore<double>& c, const double* b, double* x, double rtol, double atol,
                            cudaStream_t s) {
   const Args<double> a = make_args(c, x);
-  if (c.A.long_rows)
+  if (c.S.n > 0) {
+    const int g = c.grid_spmv;
+    switch (c.S.npts) {
+      case 5: setup_stencil_kernel<5><<<g, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+      case 7: setup_stencil_kernel<7><<<g, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+      case 9: setup_stencil_kernel<9><<<g, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+      case 27: setup_stencil_kernel<27><<<g, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+      default: setup_stencil_kernel<0><<<g, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
+    }
+  } else if (c.A.long_rows)
     setup_kernel<true><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
   else
     setup_kernel<false><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);

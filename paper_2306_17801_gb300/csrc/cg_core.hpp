@@ -11,6 +11,7 @@
 #include "apcg_internal.hpp"
 #include "cg_internal.hpp"
 #include "sell.cuh"
+#include "stencil.cuh"
 
 namespace apcg {
 
@@ -22,6 +23,7 @@ struct CgCore {
   int32_t hist_len = 0;
   int grid_spmv = 1, grid_vec = 1;
   dev::SellView<T> A;     // sliced-ELL copy of the matrix (values in T)
+  dev::StencilView S;     // or the stencil operator (matrix-free plans: S.n == n > 0)
   T* dinv = nullptr;
   T* r = nullptr;
   T* p = nullptr;

@@ -7,6 +7,7 @@
 
 #include "apcg_internal.hpp"
 #include "cluster_cg.hpp"
+#include "stencil.cuh"
 
 namespace apcg {
 
@@ -31,6 +32,12 @@ struct CgState {
 
 // Launch the A0 kernel dinv = 1 / diag(A) (flags bad diagonals on ctx).
 apcg_status launch_jacobi_setup(apcg_ctx ctx, apcg_mat A, double* dinv);
+// y[0..n) = v on ctx's stream.
+apcg_status launch_fill(apcg_ctx ctx, double* y, int64_t n, double v);
+
+// The device description of a stencil operator (stencil.cu) and its centre weight (0 if it has no centre term).
+const dev::StencilView& stencil_view(const apcg_stencil_s* S);
+double stencil_center(const apcg_stencil_s* S);
 
 // The library context used by entry points that take host buffers.
 apcg_ctx host_api_ctx();

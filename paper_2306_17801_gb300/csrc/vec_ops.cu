@@ -176,6 +176,13 @@ apcg_status same_len(apcg_vec a, apcg_vec b) {
 
 }  // namespace
 
+apcg_status launch_fill(apcg_ctx ctx, double* y, int64_t n, double v) {
+  copy_set_kernel<<<vec_grid(ctx, n >> 1, 1 << 20), kVecThreads, 0, ctx->stream>>>(n, y, nullptr, v);
+  APCG_CUDA(cudaGetLastError());
+  count_kernels(1);
+  return APCG_OK;
+}
+
 apcg_status launch_jacobi_setup(apcg_ctx ctx, apcg_mat A, double* dinv) {
   APCG_TRY(ensure_scratch(ctx));
   const int g = vec_grid(ctx, A->nrows, 1 << 20);
