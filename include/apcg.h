@@ -473,6 +473,61 @@ APCG_API apcg_status apcg_ir_plan_destroy(apcg_ir_plan plan);
 APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
                                    const apcg_ir_opts* opts, apcg_ir_result* res);
 
+/* ------------------------------------------------------------------ scalar expressions (Eval) */
+
+/*
+ * Scalar expressions over managed scalars, evaluated on the device: the C-ABI
+ * form of the expression templates and Eval() of Sec. 3.2.1 (templates
+ * cannot cross a C interface).  An expression is a postfix list of terms:
+ * APCG_EX_SCALAR pushes a managed scalar, APCG_EX_CONST a constant, a binary
+ * operator pops b then a and pushes (a op b), a unary one pops a and pushes
+ * op(a).  MIN/MAX follow fmin/fmax (a NaN operand yields the other one).
+ *
+ * apcg_expr_create "freezes" the expression (what Eval does): equal
+ * subexpressions become one instruction (common-subexpression elimination),
+ * subtrees of constants are folded where the host result equals the
+ * device's (+ - * / sqrt neg recip abs min max; never sin cos exp log), and
+ * only rewrites that keep every value are applied (x*1, 1*x, x/1, x-0, -(-x)).
+ * Limits: at most 64 instructions after freezing and 16 distinct scalars;
+ * the terms must leave exactly one value.  The expression references its
+ * scalars (not copied); they must outlive its executions.
+ */
+typedef enum {
+  APCG_EX_SCALAR = 0,
+  APCG_EX_CONST = 1,
+  APCG_EX_ADD = 2,
+  APCG_EX_SUB = 3,
+  APCG_EX_MUL = 4,
+  APCG_EX_DIV = 5,
+  APCG_EX_MIN = 6,
+  APCG_EX_MAX = 7,
+  APCG_EX_NEG = 8,
+  APCG_EX_RECIP = 9,
+  APCG_EX_SQRT = 10,
+  APCG_EX_ABS = 11,
+  APCG_EX_SIN = 12,
+  APCG_EX_COS = 13,
+  APCG_EX_EXP = 14,
+  APCG_EX_LOG = 15
+} apcg_expr_op;
+
+typedef struct {
+  int32_t op;     /* apcg_expr_op */
+  int32_t pad;
+  apcg_scalar s;  /* APCG_EX_SCALAR: the operand */
+  double c;       /* APCG_EX_CONST: the value */
+} apcg_expr_term;
+
+typedef struct apcg_expr_s* apcg_expr;
+APCG_API apcg_status apcg_expr_create(const apcg_expr_term* terms, int32_t nterms, apcg_expr* out);
+APCG_API apcg_status apcg_expr_destroy(apcg_expr expr);
+/* The frozen program: instruction and input counts, and (if text != NULL) one line per instruction. */
+APCG_API apcg_status apcg_expr_describe(apcg_expr expr, int32_t* ninstr, int32_t* ninputs, char* text, size_t cap);
+/* out := expr, one kernel launch (Execute of Sec. 3.2.1).  Marks the inputs read and out written. */
+APCG_API apcg_status apcg_expr_execute_async(apcg_ctx ctx, apcg_expr expr, apcg_scalar out);
+/* y += expr * x with the expression evaluated inside the AXPY kernel (no launch of its own). */
+APCG_API apcg_status apcg_vec_axpy_expr_async(apcg_ctx ctx, apcg_vec y, apcg_expr expr, apcg_vec x);
+
 /* ------------------------------------------------------------------ matrix-free stencil operators */
 
 /*

@@ -18,3 +18,4 @@ from .oracle import (  # noqa: F401
     pcg_f32,
     ir,
 )
+from .expr_oracle import expr_eval  # noqa: F401

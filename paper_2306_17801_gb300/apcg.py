@@ -129,6 +129,14 @@ class IrResult(C.Structure):
         }
 
 
+class ExprTerm(C.Structure):
+    _fields_ = [("op", C.c_int32), ("pad", C.c_int32), ("s", C.c_void_p), ("c", C.c_double)]
+
+
+EXPR_OPS = {name: i for i, name in enumerate(
+    ["scalar", "const", "add", "sub", "mul", "div", "min", "max", "neg", "recip", "sqrt", "abs", "sin", "cos", "exp", "log"])}
+
+
 class BatchResult(C.Structure):
     _fields_ = [
         ("iters", C.c_int32),
@@ -215,6 +223,11 @@ PROTOS = {
     "apcg_ir_plan_solve": [P, P, P, C.POINTER(IrResult)],
     "apcg_ir_plan_destroy": [P],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
+    "apcg_expr_create": [P, i32, PP],
+    "apcg_expr_destroy": [P],
+    "apcg_expr_describe": [P, P, P, C.c_char_p, C.c_size_t],
+    "apcg_expr_execute_async": [P, P, P],
+    "apcg_vec_axpy_expr_async": [P, P, P, P],
     "apcg_stencil_create": [i32, i32, i32, i32, P, P, PP],
     "apcg_stencil_destroy": [P],
     "apcg_stencil_apply_async": [P, P, P, P],
@@ -460,6 +473,28 @@ def cg_solve_host(rowptr, col, val, b, x, opts: CgOpts) -> dict:
         C.byref(res),
     )
     return res.as_dict()
+
+
+def expr_create(terms, scalars: dict):
+    """Freeze a postfix expression: terms like ("scalar", name), ("const", c), ("add",), ... ;
+    scalars maps names to apcg_scalar handles."""
+    arr = (ExprTerm * len(terms))()
+    for i, t in enumerate(terms):
+        arr[i].op = EXPR_OPS[t[0]]
+        if t[0] == "scalar":
+            arr[i].s = scalars[t[1]]
+        elif t[0] == "const":
+            arr[i].c = float(t[1])
+    h = _out()
+    call("apcg_expr_create", arr, len(terms), C.byref(h))
+    return h.value
+
+
+def expr_describe(expr) -> dict:
+    ni, nl = C.c_int32(), C.c_int32()
+    buf = C.create_string_buffer(8192)
+    call("apcg_expr_describe", C.c_void_p(expr), C.byref(ni), C.byref(nl), buf, len(buf))
+    return {"instructions": ni.value, "inputs": nl.value, "text": buf.value.decode()}
 
 
 def stencil_create(dims, offsets, weights):
