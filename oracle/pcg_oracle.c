@@ -25,7 +25,9 @@
  *     z = r ./ d;  rho_new = (r,z);  beta = rho_new / rho
  *     p = z + beta p;  rho = rho_new
  *
- * The test "sqrt(rr) <= tol" is also applied once before the loop (i = 0).
+ * The test "sqrt(rr) <= tol" is also applied once before the loop (i = 0),
+ * after a check that rr and bn are finite (a NaN or infinity in b or x0 is a
+ * breakdown, not convergence against an infinite tolerance).
  * Every inner product uses Neumaier-compensated summation in the working
  * precision, so the oracle is at least as accurate as any GPU reduction tree.
  *
@@ -171,6 +173,10 @@ int oracle_pcg(int64_t n, const int32_t* rowptr, const int32_t* col, const doubl
   if (atol > tol) tol = atol;
   res->bnorm = bn;
   res->rr = rr;
+  if (!isfinite(rr) || !isfinite(bn)) { /* a non-finite b or x0: the tolerance would be meaningless */
+    status = OR_BREAKDOWN;
+    goto done;
+  }
   if (sqrt(rr) <= tol) {
     status = OR_CONVERGED;
     goto done;
@@ -340,6 +346,10 @@ int oracle_ir(int64_t n, const int32_t* rowptr, const int32_t* col, const double
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
     double rn = sqrt(oracle_dot(n, r, r));
     res->rel_res = bn > 0.0 ? rn / bn : rn;
+    if (!isfinite(rn) || !isfinite(bn)) {
+      status = OR_BREAKDOWN;
+      break;
+    }
     if (rn <= rtol * bn) {
       status = OR_CONVERGED;
       break;

@@ -17,7 +17,7 @@
  *
  *   r0 = D^-1 (b - A x0);  u = w = r* = r0;  v = p = M u;  d = 0
  *   tau = ||r0||;  theta = eta = 0;  rho = (r*, r0);  bn = ||D^-1 b||
- *   stop (converged) if tau <= tol = max(rtol * bn, atol)
+ *   breakdown if tau or bn is not finite; stop (converged) if tau <= tol = max(rtol * bn, atol)
  *   iteration i = 1, 2, ...:
  *     sigma = (v, r*);  sigma == 0 or not finite -> breakdown
  *     alpha = rho / sigma
@@ -127,7 +127,9 @@ int oracle_tfqmr(int64_t n, const int32_t* rowptr, const int32_t* col, const dou
   res->bnorm = bn;
   int reason = TQ_NOT_CONVERGED;
   int32_t it = 0;
-  if (tau <= tol) {
+  if (!isfinite(tau) || !isfinite(bn)) { /* a non-finite b or x0 */
+    reason = TQ_BREAKDOWN;
+  } else if (tau <= tol) {
     reason = TQ_CONVERGED;
   } else {
     for (it = 1;; ++it) {

@@ -207,6 +207,15 @@ apcg_status finish_async(apcg_cg_plan P) {
   return APCG_OK;
 }
 
+apcg_status check_vectors(int32_t n, apcg_vec b, apcg_vec x) {
+  APCG_CHECK(b && x, "b or x is NULL");
+  APCG_CHECK(b->dtype == APCG_F64 && x->dtype == APCG_F64, "b and x must be float64");
+  APCG_CHECK(b->n == n && x->n == n, "b/x length differs from the matrix size %d", n);
+  APCG_CHECK(n == 0 || (aligned16(b->dptr) && aligned16(x->dptr)), "b/x must be 16-byte aligned");
+  APCG_CHECK(b->dptr != x->dptr || n == 0, "b and x must not alias");
+  return APCG_OK;
+}
+
 apcg_status check_solve_args(apcg_cg_plan P, apcg_vec b, apcg_vec x) {
   APCG_CHECK(P, "plan is NULL");
   APCG_CHECK(b && x, "b or x is NULL");
@@ -495,7 +504,8 @@ apcg_status apcg_cg_plan_profile(apcg_cg_plan P, apcg_vec b, apcg_vec x, int32_t
 
 apcg_status apcg_cg_solve(apcg_ctx ctx_in, apcg_mat A, apcg_vec b, apcg_vec x, const apcg_cg_opts* opts,
                           apcg_cg_result* res) {
-  APCG_CHECK(res, "res is NULL");
+  APCG_CHECK(res && A, "NULL argument");
+  APCG_TRY(check_vectors(A->nrows, b, x));  // before the plan does any work
   apcg_cg_plan P = nullptr;
   APCG_TRY(apcg_cg_plan_create(ctx_in, A, opts, &P));
   apcg_status st = apcg_cg_plan_solve(P, b, x, res);

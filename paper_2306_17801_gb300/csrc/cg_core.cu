@@ -126,7 +126,8 @@ __device__ __forceinline__ void setup_body(const Args<double>& a, const double* 
     st->hist_len = hist_len;
     st->body_runs = 0;
     st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
-    st->done = (sqrt(tot[1]) <= tol) ? kDoneConverged : 0;
+    // a non-finite b or x0 is a breakdown, not convergence against an infinite tolerance
+    st->done = (!isfinite(tot[1]) || !isfinite(tot[2])) ? kDoneBreakdown : (sqrt(tot[1]) <= tol) ? kDoneConverged : 0;
   }
 }
 

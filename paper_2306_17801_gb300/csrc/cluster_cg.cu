@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(ClusterArgs
     int it = 0, done = 0;
     if (v[3] > 0.0)
       done = kDoneBadDiagonal;
+    else if (!isfinite(rr) || !isfinite(bb))  // a non-finite b or x0
+      done = kDoneBreakdown;
     else if (sqrt(rr) <= tol)
       done = kDoneConverged;
     else
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kClusterThreads, (R >= 8 ? 1 : 2)) cg_cluster_
       clu::cluster_sum<2>(v, S, parity, cl);
       rr64 = v[0];
       bb = v[1];
-      if (!isfinite(rr64)) {
+      if (!isfinite(rr64) || !isfinite(bb)) {
         done = kDoneBreakdown;
         break;
       }

@@ -143,7 +143,9 @@ __global__ void __launch_bounds__(kThreads) s1_kernel(TqArgs a, const double* __
     st->check_every = k;
     st->hist_len = hist_len;
     st->body_runs = 0;
-    st->done = st->tau <= st->tol ? kDoneConverged : 0;
+    st->done = (!isfinite(tot[0]) || !isfinite(tot[1])) ? kDoneBreakdown  // a non-finite b or x0
+               : st->tau <= st->tol                          ? kDoneConverged
+                                                             : 0;
   }
 }
 

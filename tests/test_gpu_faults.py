@@ -1,0 +1,150 @@
+"""Failure detection with faults injected on the host (nothing faults, traps or hangs the GPU).
+
+A NaN or infinity in the right-hand side or the start vector must end every
+solver and mode with a reported breakdown (not a hang, not a CUDA error), a
+NaN system inside a batch must fail alone, bad arguments must be rejected
+before anything is enqueued, and the context must stay usable for the next
+solve.  The library has no device-side spin-waits, so no kernel can wait on a
+flag that is never set.
+"""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from synthetic import batch_aniso_7pt, batch_shifted_5pt, laplace_2d_5pt, rhs_from_solution, stencil_terms
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2306_17801_gb300 import apcg  # noqa: E402
+
+V = C.c_void_p
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    apcg.load()
+    c = apcg.ctx_create()
+    yield c
+    apcg.call("apcg_ctx_destroy", V(c))
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _system(N=30):
+    A = laplace_2d_5pt(N, shift=0.1)
+    b = rhs_from_solution(A, np.random.default_rng(1).uniform(-1, 1, A.n))
+    return A, b
+
+
+def _cg(ctx, A, b, x0=None, solver="cg", **kw):
+    rowptr, col, val, bt = _t(A.rowptr), _t(A.col), _t(A.val), _t(b)
+    x = _t(np.zeros(A.n) if x0 is None else x0)
+    M = apcg.mat_wrap(rowptr, col, val)
+    vb, vx = apcg.vec_wrap(bt), apcg.vec_wrap(x)
+    try:
+        fn = apcg.cg_solve if solver == "cg" else apcg.tfqmr_solve
+        return fn(ctx, M, vb, vx, apcg.cg_opts(**kw)), x.cpu().numpy()
+    finally:
+        for h, f in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (M, "apcg_mat_destroy")):
+            apcg.call(f, V(h))
+
+
+@pytest.mark.parametrize("mode", ["host_sync", "async", "async_graph", "persistent"])
+@pytest.mark.parametrize("where", ["b_nan", "b_inf", "x0_nan"])
+def test_cg_reports_breakdown_on_non_finite_input(ctx, mode, where):
+    A, b = _system()
+    x0 = None
+    if where == "b_nan":
+        b = b.copy()
+        b[17] = np.nan
+    elif where == "b_inf":
+        b = b.copy()
+        b[3] = np.inf
+    else:
+        x0 = np.zeros(A.n)
+        x0[5] = np.nan
+    res, _ = _cg(ctx, A, b, x0=x0, mode=mode, rtol=1e-8, max_it=500)
+    assert res["reason"] == "breakdown" and res["iters"] <= 1, res
+    # the context is still usable
+    A2, b2 = _system(12)
+    ok, _ = _cg(ctx, A2, b2, mode=mode, rtol=1e-8)
+    assert ok["reason"] == "converged"
+
+
+@pytest.mark.parametrize("mode", ["host_sync", "async_graph"])
+def test_tfqmr_reports_breakdown_on_nan(ctx, mode):
+    A, b = _system()
+    b = b.copy()
+    b[0] = np.nan
+    res, _ = _cg(ctx, A, b, solver="tfqmr", mode=mode, rtol=1e-8, max_it=500)
+    assert res["reason"] == "breakdown"
+    ok, _ = _cg(ctx, *_system(12), solver="tfqmr", mode=mode, rtol=1e-8)
+    assert ok["reason"] == "converged"
+
+
+def test_stencil_cg_reports_breakdown_on_nan(ctx):
+    dims = (20, 20, 1)
+    offs, w = stencil_terms("5pt", dims)
+    S = apcg.stencil_create(dims, offs, w)
+    plan = apcg.cg_plan_create_stencil(ctx, S, apcg.cg_opts(rtol=1e-8, mode="async_graph", max_it=300))
+    apcg.call("apcg_stencil_destroy", V(S))
+    b = np.ones(400)
+    b[7] = np.nan
+    bt, x = _t(b), torch.zeros(400, dtype=torch.float64, device="cuda:0")
+    vb, vx = apcg.vec_wrap(bt), apcg.vec_wrap(x)
+    res = apcg.cg_plan_solve(plan, vb, vx)
+    assert res["reason"] == "breakdown"
+    apcg.call("apcg_cg_plan_destroy", V(plan))
+    for h in (vb, vx):
+        apcg.call("apcg_vec_destroy", V(h))
+
+
+@pytest.mark.parametrize("ir", [False, True])
+def test_batched_nan_system_fails_alone(ctx, ir):
+    B = batch_aniso_7pt(9, seed=3, side_lo=4, side_hi=10) if ir else batch_shifted_5pt(9, seed=3, side_lo=8, side_hi=30)
+    b = B.b.copy()
+    bad = 4
+    b[int(B.sys_row_off[bad]) + 2] = np.nan
+    rowptr, col, bt = _t(B.rowptr), _t(B.col), _t(b)
+    x = torch.zeros(B.n_total, dtype=torch.float64, device="cuda:0")
+    if ir:
+        plan = apcg.batch_ir_plan_create(ctx, B.sys_row_off, rowptr, col, None, _t(B.val.astype(np.float32)),
+                                         apcg.ir_opts(rtol=1e-10))
+    else:
+        plan = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, _t(B.val), apcg.cg_opts(rtol=1e-8))
+    res = apcg.batch_plan_solve(plan, bt, x, B.nsys)
+    apcg.call("apcg_batch_plan_destroy", V(plan))
+    for s, r in enumerate(res):
+        assert r["reason"] == ("breakdown" if s == bad else "converged"), (s, r)
+
+
+def test_bad_arguments_are_rejected_before_enqueue(ctx):
+    A, b = _system(10)
+    rowptr, col, val, bt = _t(A.rowptr), _t(A.col), _t(A.val), _t(b)
+    M = apcg.mat_wrap(rowptr, col, val)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda:0")
+    vb, vx = apcg.vec_wrap(bt), apcg.vec_wrap(x)
+    short = torch.zeros(A.n - 1, dtype=torch.float64, device="cuda:0")
+    vs = apcg.vec_wrap(short)
+    apcg.reset_counters()
+    with pytest.raises(apcg.ApcgError):  # wrong length
+        apcg.cg_solve(ctx, M, vs, vx, apcg.cg_opts())
+    with pytest.raises(apcg.ApcgError):  # aliasing b and x
+        apcg.cg_solve(ctx, M, vb, vb, apcg.cg_opts())
+    with pytest.raises(apcg.ApcgError):  # bad option
+        apcg.cg_solve(ctx, M, vb, vx, apcg.cg_opts(check_every=0))
+    assert apcg.get_counters()["kernel_launches"] == 0
+    res = apcg.cg_solve(ctx, M, vb, vx, apcg.cg_opts(rtol=1e-8))
+    assert res["reason"] == "converged"
+    for h, f in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (vs, "apcg_vec_destroy"), (M, "apcg_mat_destroy")):
+        apcg.call(f, V(h))

@@ -359,3 +359,20 @@ def test_pins_catch_planted_mistakes(orc):
     for m in (1, 2, 3, 4, 5, 6):
         got = _pins_pass(orc, m)
         assert not all(got.values()), f"mutation {m} went unnoticed: {got}"
+
+
+def test_non_finite_inputs_are_breakdowns(orc):
+    """A NaN or infinity in b or x0 ends every oracle solver with a breakdown (reading 10), never with
+    convergence against an infinite tolerance."""
+    from synthetic import laplace_2d_5pt
+
+    A = laplace_2d_5pt(8)
+    for bad in (np.nan, np.inf, -np.inf):
+        b = np.ones(A.n)
+        b[5] = bad
+        assert orc.pcg(A, b)["reason"] == "breakdown"
+        assert orc.tfqmr(A, b)["reason"] == "breakdown"
+        assert orc.ir(A, b)["reason"] == "breakdown"
+        x0 = np.zeros(A.n)
+        x0[2] = bad
+        assert orc.pcg(A, np.ones(A.n), x0=x0)["reason"] == "breakdown"
