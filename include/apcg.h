@@ -563,6 +563,17 @@ APCG_API apcg_status apcg_stencil_apply_async(apcg_ctx ctx, apcg_stencil stencil
  */
 APCG_API apcg_status apcg_cg_plan_create_stencil(apcg_ctx ctx, apcg_stencil stencil, const apcg_cg_opts* opts,
                                                  apcg_cg_plan* out);
+/*
+ * Mixed-precision refinement (the scheme of apcg_ir_plan_create) on a stencil
+ * operator: the float64 outer residual uses the float64 weights, the float32
+ * inner Jacobi-PCG the weights rounded to float32 and the Jacobi diagonal
+ * 1 / (float) centre.  Without matrix arrays an inner iteration moves only
+ * float32 vectors.  Solve and destroy with apcg_ir_plan_solve/destroy.
+ * APCG_ERR_BAD_DIAGONAL if the centre term is missing, zero or not finite
+ * (in float64 or float32).
+ */
+APCG_API apcg_status apcg_ir_plan_create_stencil(apcg_ctx ctx, apcg_stencil stencil, const apcg_ir_opts* opts,
+                                                 apcg_ir_plan* out);
 
 /* ------------------------------------------------------------------ TFQMR */
 

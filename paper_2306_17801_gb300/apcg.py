@@ -232,6 +232,7 @@ PROTOS = {
     "apcg_stencil_destroy": [P],
     "apcg_stencil_apply_async": [P, P, P, P],
     "apcg_cg_plan_create_stencil": [P, P, C.POINTER(CgOpts), PP],
+    "apcg_ir_plan_create_stencil": [P, P, C.POINTER(IrOpts), PP],
     "apcg_tfqmr_plan_create": [P, P, C.POINTER(CgOpts), PP],
     "apcg_tfqmr_plan_solve": [P, P, P, C.POINTER(CgResult)],
     "apcg_tfqmr_plan_destroy": [P],
@@ -512,6 +513,12 @@ def stencil_create(dims, offsets, weights):
 def cg_plan_create_stencil(ctx, stencil, opts: CgOpts):
     h = _out()
     call("apcg_cg_plan_create_stencil", C.c_void_p(ctx), C.c_void_p(stencil), C.byref(opts), C.byref(h))
+    return h.value
+
+
+def ir_plan_create_stencil(ctx, stencil, opts: IrOpts):
+    h = _out()
+    call("apcg_ir_plan_create_stencil", C.c_void_p(ctx), C.c_void_p(stencil), C.byref(opts), C.byref(h))
     return h.value
 
 

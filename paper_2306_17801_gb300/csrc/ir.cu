@@ -40,6 +40,7 @@ struct apcg_ir_plan_s {
   apcg_id id_a64 = 0, id_a32 = 0, id = 0;
   apcg::dev::SellView<double> A64;  // outer residual values (nslices == 0 when absent)
   apcg::dev::SellView<float> A32;   // inner values (also the outer ones when A64 is absent)
+  apcg::dev::StencilView S;         // or a stencil operator (S.n > 0): float64 weights outside, float32 inside
   apcg::CgCore<float> core;         // inner solver; its x is d32
   float* d32 = nullptr;
   IrState* ost = nullptr;
@@ -87,6 +88,18 @@ apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cu
   a.rtol_inner = P->opts.rtol_inner;
   a.max_inner = P->core.max_it;
   a.inner_k = P->core.k;
+  if (P->S.n > 0) {
+    const int g = P->grid_res;
+    switch (P->S.npts) {
+      case 5: ir::residual_stencil_kernel<5><<<g, kThreads, 0, s>>>(a, P->S); break;
+      case 7: ir::residual_stencil_kernel<7><<<g, kThreads, 0, s>>>(a, P->S); break;
+      case 9: ir::residual_stencil_kernel<9><<<g, kThreads, 0, s>>>(a, P->S); break;
+      case 27: ir::residual_stencil_kernel<27><<<g, kThreads, 0, s>>>(a, P->S); break;
+      default: ir::residual_stencil_kernel<0><<<g, kThreads, 0, s>>>(a, P->S); break;
+    }
+    APCG_CUDA(cudaGetLastError());
+    return APCG_OK;
+  }
   const bool lg = P->A32.long_rows != 0;
   if (P->outer64) {
     if (lg)
@@ -248,6 +261,85 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   APCG_CUDA(cudaStreamSynchronize(ctx->stream));
   counters().host_syncs++;
   APCG_TRY(ctx_check_device_error(ctx));
+  APCG_TRY(core_build_graph(c, P->d32, ctx->stream));
+  *out = P.release();
+  return APCG_OK;
+}
+
+apcg_status apcg_ir_plan_create_stencil(apcg_ctx ctx_in, apcg_stencil St, const apcg_ir_opts* opts,
+                                        apcg_ir_plan* out) {
+  APCG_CHECK(out && St, "NULL argument");
+  const double center = stencil_center(St);
+  if (!(center != 0.0) || !std::isfinite(center) || !((float)center != 0.0f) || !std::isfinite((float)center))
+    return set_error(APCG_ERR_BAD_DIAGONAL, "Jacobi: the stencil's centre weight is missing, zero or not finite");
+  apcg_ir_opts o;
+  if (opts)
+    o = *opts;
+  else
+    apcg_ir_opts_default(&o);
+  if (o.max_outer <= 0) o.max_outer = 50;
+  if (o.max_inner <= 0) o.max_inner = 1000;
+  if (!(o.rtol_inner > 0.0f)) o.rtol_inner = 1e-4f;
+  if (o.inner_check_every < 1) o.inner_check_every = 1;
+  APCG_CHECK(o.rtol >= 0.0 && o.atol >= 0.0, "tolerances must be non-negative");
+  apcg_ctx ctx;
+  APCG_TRY(resolve_ctx(ctx_in, &ctx));
+  std::unique_ptr<apcg_ir_plan_s, void (*)(apcg_ir_plan)> P(new apcg_ir_plan_s(), ir_destroy);
+  P->ctx = ctx;
+  P->opts = o;
+  P->S = stencil_view(St);
+  P->n = P->S.n;
+  P->nnz = (int64_t)P->S.npts * P->S.n;
+  P->outer64 = true;
+  CgCore<float>& c = P->core;
+  c.n = P->n;
+  c.k = o.inner_check_every;
+  c.max_it = o.max_inner;
+  c.hist_len = 0;
+  c.S = P->S;
+  const int sms = ctx_num_sms(ctx);
+  core_configure(c, P->nnz, sms);
+  P->grid_res = c.grid_spmv;
+  P->grid_upd = std::max(1, std::min(sms * 8, (int)((P->n / 4 + kThreads - 1) / kThreads)));
+  // Workspace: dinv32, r, p, w, z, d (float32); partials and states.
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nv = up(sizeof(float) * (size_t)(P->n > 0 ? P->n : 1));
+  const size_t nip = up(sizeof(float) * dev::kMaxPartials * 3);
+  const size_t nop = up(sizeof(double) * dev::kMaxPartials * 2);
+  const size_t nst = up(sizeof(CgState)) + up(sizeof(IrState));
+  const size_t total = 6 * nv + nip + nop + nst;
+  char* ws = nullptr;
+  APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
+  P->ws = ws;
+  c.dinv = reinterpret_cast<float*>(ws);
+  c.r = reinterpret_cast<float*>(ws + nv);
+  c.p = reinterpret_cast<float*>(ws + 2 * nv);
+  c.w = reinterpret_cast<float*>(ws + 3 * nv);
+  c.z = reinterpret_cast<float*>(ws + 4 * nv);
+  P->d32 = reinterpret_cast<float*>(ws + 5 * nv);
+  char* q = ws + 6 * nv;
+  c.partials = reinterpret_cast<float*>(q);
+  P->opartials = reinterpret_cast<double*>(q + nip);
+  c.st = reinterpret_cast<CgState*>(q + nip + nop);
+  P->ost = reinterpret_cast<IrState*>(q + nip + nop + up(sizeof(CgState)));
+  APCG_CUDA(cudaMemsetAsync(q, 0, nip + nop + nst, ctx->stream));
+  APCG_CUDA(cudaMallocHost(&P->host_state, sizeof(IrState) + sizeof(CgState)));
+  {
+    std::lock_guard<std::mutex> g(global_mutex());
+    P->id = register_memory(ws, total);
+  }
+  OpScope op(ctx);
+  op.write(P->id);
+  APCG_TRY(op.begin());
+  if (P->n > 0) {
+    const int g = std::max(1, std::min(sms * 8, (int)((P->n + kThreads - 1) / kThreads)));
+    ir::fill32_kernel<<<g, kThreads, 0, ctx->stream>>>(c.dinv, P->n, 1.0f / (float)center);
+    APCG_CUDA(cudaGetLastError());
+    count_kernels(1);
+  }
+  APCG_TRY(op.finish());
+  APCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  counters().host_syncs++;
   APCG_TRY(core_build_graph(c, P->d32, ctx->stream));
   *out = P.release();
   return APCG_OK;

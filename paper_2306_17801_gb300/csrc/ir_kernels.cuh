@@ -10,6 +10,7 @@
 #include "cg_internal.hpp"
 #include "kernels_common.cuh"
 #include "sell.cuh"
+#include "stencil.cuh"
 
 namespace apcg {
 namespace ir {
@@ -58,13 +59,14 @@ struct ResidualArgs {
 // r = b - A x in float64 (values TV widened to double), ||r||^2 and ||b||^2 in
 // float64; then the inner set-up in float32: r32 = (float) r, p = z = D32^-1 r32,
 // d = 0, rho = (r32, z), (r32, r32) and the inner tolerance.
-template <bool LONG, class TV>
-__global__ void __launch_bounds__(kThreads) residual_kernel(ResidualArgs a, dev::SellView<TV> A) {
+// spmv(epi) applies the float64 operator to x with the given row epilogue.
+template <class Spmv>
+__device__ __forceinline__ void residual_body(const ResidualArgs& a, Spmv spmv) {
   __shared__ double red64[2 * kThreads];
   __shared__ float red32[2 * kThreads];
   double v64[2] = {0.0, 0.0};
   float v32[2] = {0.0f, 0.0f};
-  dev::sell_spmv<false, LONG, double>(A, a.x, [&](int32_t i, double ax, double) {
+  spmv([&](int32_t i, double ax, double) {
     const double bi = __ldg(a.b + i);
     const double ri = bi - ax;
     v64[0] = fma(ri, ri, v64[0]);
@@ -98,6 +100,23 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(ResidualArgs a, dev:
     st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
     st->done = (sqrtf(t32[1]) <= tol) ? kDoneConverged : 0;
   }
+}
+
+template <bool LONG, class TV>
+__global__ void __launch_bounds__(kThreads) residual_kernel(ResidualArgs a, dev::SellView<TV> A) {
+  residual_body(a, [&](auto epi) { dev::sell_spmv<false, LONG, double>(A, a.x, epi); });
+}
+
+// The same on a stencil operator (float64 weights).
+template <int NP>
+__global__ void __launch_bounds__(kThreads) residual_stencil_kernel(ResidualArgs a, dev::StencilView S) {
+  residual_body(a, [&](auto epi) { dev::stencil_spmv<NP, false, double>(S, a.x, epi); });
+}
+
+// y[0..n) = v (float32).
+__global__ void __launch_bounds__(kThreads) fill32_kernel(float* __restrict__ y, int64_t n, float v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = v;
 }
 
 // x += (double) d.

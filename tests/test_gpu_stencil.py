@@ -171,3 +171,50 @@ def test_stencil_cg_full_size_128cube(ctx):
     res, x = _stencil_cg(ctx, "7pt", (128, 128, 128), p.b, rtol=1e-8, check_every=10, mode="async_graph",
                          max_it=5000)
     _check(res, x, ref, 10)
+
+
+def _stencil_ir(ctx, kind, dims, b, shift=0.0, **kw):
+    offs, w = stencil_terms(kind, dims, shift=shift)
+    S = apcg.stencil_create(dims, offs, w)
+    plan = apcg.ir_plan_create_stencil(ctx, S, apcg.ir_opts(**kw))
+    apcg.call("apcg_stencil_destroy", V(S))
+    bt = _t(b)
+    x = torch.zeros_like(bt)
+    vb, vx = apcg.vec_wrap(bt), apcg.vec_wrap(x)
+    res = apcg.ir_plan_solve(plan, vb, vx)
+    apcg.call("apcg_ir_plan_destroy", V(plan))
+    for h in (vb, vx):
+        apcg.call("apcg_vec_destroy", V(h))
+    return res, x.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind,dims,shift", [("5pt", (41, 37, 1), 0.0), ("9pt", (31, 31, 1), 0.0),
+                                             ("7pt", (17, 19, 13), 0.0), ("27pt", (11, 11, 11), 0.5)])
+def test_stencil_refinement_reaches_double_accuracy(ctx, kind, dims, shift):
+    import scipy.linalg as sla
+
+    A = stencil_matrix(kind, dims, shift=shift)
+    b = rhs_from_solution(A, np.random.default_rng(8).uniform(-1, 1, A.n))
+    res, x = _stencil_ir(ctx, kind, dims, b, shift=shift, rtol=1e-10, rtol_inner=1e-4, inner_check_every=1)
+    assert res["reason"] == "converged" and res["outer"] >= 1
+    true_rel = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= 1.05e-10 and abs(true_rel - res["rel_res"]) <= 1e-12
+    D = A.to_dense()
+    xc = sla.cho_solve(sla.cho_factor(D), b)
+    kappa = np.linalg.cond(D)
+    assert np.linalg.norm(x - xc) / np.linalg.norm(xc) <= kappa * 2e-10
+    ref = oracle.ir(A, b, rtol=1e-10)
+    assert ref["reason"] == "converged" and abs(ref["outer"] - res["outer"]) <= 1
+
+
+def test_stencil_refinement_full_size_128cube(ctx):
+    """128^3 7-point refined to 1e-10 against the float64 stencil CG to 1e-10."""
+    p = single_problem("c2", seed=0)
+    res, x_ir = _stencil_ir(ctx, "7pt", (128, 128, 128), p.b, rtol=1e-10, inner_check_every=10)
+    assert res["reason"] == "converged"
+    rel_ir = np.linalg.norm(p.b - oracle.spmv(p.A, x_ir)) / np.linalg.norm(p.b)
+    assert rel_ir <= 1.05e-10
+    r64, x64 = _stencil_cg(ctx, "7pt", (128, 128, 128), p.b, rtol=1e-10, check_every=10, mode="async_graph",
+                           max_it=10000)
+    assert r64["reason"] == "converged"
+    assert np.linalg.norm(x_ir - x64) / np.linalg.norm(x64) <= 1e-6
