@@ -312,12 +312,7 @@ typedef enum {
   /* The whole solve in one kernel on one thread block (small systems). */
   APCG_MODE_PERSISTENT = 3,
   /* Library choice: PERSISTENT for small systems, ASYNC_GRAPH otherwise. */
-  APCG_MODE_AUTO = 4,
-  /* The whole iteration loop in one cooperative launch over the GPU: the
-     kernels' phases separated by grid-wide barriers (bounded waits; one that
-     runs out makes the solve return APCG_ERR_TIMEOUT) instead of kernel
-     boundaries.  CSR plans only. */
-  APCG_MODE_GRID = 5
+  APCG_MODE_AUTO = 4
 } apcg_mode;
 
 typedef enum {

@@ -33,7 +33,7 @@ READ, WRITE, READ_WRITE = 1, 2, 3
 JOIN_DESTROY, JOIN_SYNC, JOIN_NO_SYNC = 0, 1, 2
 F64, F32 = 0, 1
 MODE_HOST_SYNC, MODE_ASYNC, MODE_ASYNC_GRAPH, MODE_PERSISTENT, MODE_AUTO = 0, 1, 2, 3, 4
-MODES = {"host_sync": 0, "async": 1, "async_graph": 2, "persistent": 3, "auto": 4, "grid": 5}
+MODES = {"host_sync": 0, "async": 1, "async_graph": 2, "persistent": 3, "auto": 4}
 REASONS = {0: "converged", 1: "not_converged", 2: "breakdown"}
 
 

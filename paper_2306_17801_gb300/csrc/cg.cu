@@ -38,7 +38,6 @@ struct apcg_cg_plan_s {
   apcg_id id = 0;
   bool pending = false;
   int64_t last_launches = 0;
-  int grid_blocks = 0;  // one-launch (grid) mode
   // whole-solve cluster mode
   apcg::ClusterShape shape;
   apcg::SysDesc* sys = nullptr;
@@ -122,20 +121,6 @@ apcg_status solve_host_sync(apcg_cg_plan P, const double* b, double* x) {
   if (P->opts.beta_hist)
     for (size_t i = 0; i < bh.size(); ++i) P->opts.beta_hist[i] = bh[i];
   count_kernels(launches);
-  return APCG_OK;
-}
-
-// The one-launch form: set-up kernel, then the cooperative loop kernel.
-apcg_status enqueue_grid(apcg_cg_plan P, const double* b, double* x) {
-  cudaStream_t s = P->ctx->stream;
-  CgCore<double>& c = P->core;
-  APCG_TRY(core_setup_f64(c, b, x, P->opts.rtol, P->opts.atol, s));
-  APCG_TRY(core_grid_solve(c, x, s, P->grid_blocks));
-  count_kernels(2);
-  P->last_launches = 2;
-  APCG_CUDA(cudaMemcpyAsync(P->st_host, c.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-  counters().d2h_copies++;
-  counters().d2h_bytes += sizeof(CgState);
   return APCG_OK;
 }
 
@@ -284,9 +269,7 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
   APCG_CHECK(o.check_every >= 1, "check_every must be >= 1");
   APCG_CHECK(o.rtol >= 0.0 && o.atol >= 0.0, "tolerances must be non-negative");
   APCG_CHECK(o.history_len >= 0, "history_len must be >= 0");
-  APCG_CHECK(o.mode >= APCG_MODE_HOST_SYNC && o.mode <= APCG_MODE_GRID, "bad mode %d", o.mode);
-  if (S && o.mode == APCG_MODE_GRID)
-    return set_error(APCG_ERR_UNSUPPORTED, "the one-launch form reads a sliced-ELL matrix, not a stencil");
+  APCG_CHECK(o.mode >= APCG_MODE_HOST_SYNC && o.mode <= APCG_MODE_AUTO, "bad mode %d", o.mode);
   std::unique_ptr<apcg_cg_plan_s, apcg_status (*)(apcg_cg_plan)> P(new apcg_cg_plan_s(), cg_plan_destroy);
   P->ctx = ctx;
   if (A) {
@@ -370,10 +353,6 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
     c.A.val = sval;
     c.A.long_rows = L.long_rows;
     core_configure(c, A->nnz, ctx_num_sms(ctx));  // the SpMV kernel instance depends on the row length
-    if (P->mode == APCG_MODE_GRID) {
-      P->grid_blocks = core_grid_blocks(c, ctx_num_sms(ctx));
-      if (P->grid_blocks < 1) return set_error(APCG_ERR_UNSUPPORTED, "no cooperative grid fits this device");
-    }
   }
   SysDesc d0{};
   d0.row0 = 0;
@@ -413,8 +392,6 @@ apcg_status cg_plan_enqueue(apcg_cg_plan P, apcg_vec b, apcg_vec x) {
     st = solve_host_sync(P, bp, xp);
   else if (P->mode == APCG_MODE_PERSISTENT)
     st = enqueue_persistent(P, bp, xp);
-  else if (P->mode == APCG_MODE_GRID)
-    st = enqueue_grid(P, bp, xp);
   else
     st = enqueue_async(P, bp, xp, P->mode == APCG_MODE_ASYNC_GRAPH);
   apcg_status st2 = op.finish();
@@ -437,8 +414,6 @@ apcg_status cg_plan_finish(apcg_cg_plan P, apcg_cg_result* res) {
     if (r.done == kDoneBadDiagonal)
       return set_error(APCG_ERR_BAD_DIAGONAL, "Jacobi: a diagonal entry is missing, zero or not finite");
   }
-  if (P->mode == APCG_MODE_GRID && P->st_host->bar_err)
-    return set_error(APCG_ERR_TIMEOUT, "a bounded grid-barrier wait ran out");
   fill_result(P, res);
   return APCG_OK;
 }

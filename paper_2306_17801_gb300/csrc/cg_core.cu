@@ -124,8 +124,6 @@ __device__ __forceinline__ void setup_body(const Args<double>& a, const double* 
     st->hist_len = hist_len;
     st->body_runs = 0;
     st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
-    st->bar_count = 0;
-    st->bar_err = 0;
     // a non-finite b or x0 is a breakdown, not convergence against an infinite tolerance
     st->done = (!isfinite(tot[1]) || !isfinite(tot[2])) ? kDoneBreakdown : (sqrt(tot[1]) <= tol) ? kDoneConverged : 0;
   }
@@ -357,194 +355,6 @@ __global__ void __launch_bounds__(kThreads, 4) k3_kernel(Args<T> a, double beta_
     for (int64_t i = nv * E; i < n; ++i) a.p[i] = fma(beta, a.p[i], a.z[i]);
 }
 
-// ---------------------------------------------------------------- one-launch form
-//
-// The whole iteration loop in one cooperative launch (every block resident):
-// the three kernels' phases separated by grid-wide barriers instead of kernel
-// boundaries.  After each barrier every block adds the partial sums itself,
-// in block order, so all blocks take the same decisions (alpha, the test,
-// beta) from the same bits and no last block serialises the end of a phase.
-// Barrier waits are bounded: a wait that runs out sets st->bar_err, and every
-// block leaves the loop at its next barrier.
-
-constexpr uint32_t kBarrierPolls = 1u << 24;
-
-__device__ __forceinline__ bool grid_barrier(CgState* st, unsigned nblocks) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned* vgen = &st->bar_gen;
-    volatile int* verr = &st->bar_err;
-    const unsigned g = *vgen;
-    __threadfence();
-    if (atomicAdd(&st->bar_count, 1u) == nblocks - 1) {
-      st->bar_count = 0;
-      __threadfence();
-      atomicAdd(&st->bar_gen, 1u);
-    } else {
-      uint32_t polls = 0;
-      while (*vgen == g) {
-        if (++polls > kBarrierPolls || *verr) {
-          atomicOr(&st->bar_err, 1);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok && !*verr;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// Sum NV partial arrays of nb values each, in block order (the same bits in every block).
-template <int NV, class T>
-__device__ __forceinline__ void grid_sum_all(const T* partials, int nb, T (&tot)[NV]) {
-  __shared__ T s_tot[NV];
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      T t = T(0);
-      for (int i = threadIdx.x; i < nb; i += 32) t += __ldcg(partials + k * nb + i);
-      t = dev::warp_sum(t);
-      if (threadIdx.x == 0) s_tot[k] = t;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) tot[k] = s_tot[k];
-  __syncthreads();  // s_tot is rewritten by the next call
-}
-
-template <bool LONG, class T>
-__global__ void __launch_bounds__(kThreads, 4) grid_cg_kernel(Args<T> a) {
-  using VT = typename V16<T>::type;
-  constexpr int E = V16<T>::E;
-  __shared__ T red[2 * kThreads];
-  CgState* st = a.st;
-  const unsigned nb = gridDim.x;
-  T* part_g = a.partials;            // [nb]
-  T* part_u = a.partials + nb;       // [2 nb]
-  T rho = (T)st->rho;
-  const T tol = (T)st->tol;
-  const int32_t max_it = st->max_it, kchk = st->check_every, hist_len = st->hist_len;
-  int32_t it = st->iter;
-  int32_t done = st->done;
-  T rr = (T)st->rr, alpha = T(0), beta = T(0);
-  const int64_t n = a.n, nv = n / E, stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-  while (!done) {
-    // phase 1: w = A p, gamma = (p, w)
-    T v1[1] = {T(0)};
-    // p changes between barriers of this launch: gather it through the coherent path
-    dev::sell_spmv<true, LONG, T, true>(a.A, a.p, [&](int32_t i, T s, T p_i) {
-      a.w[i] = s;
-      v1[0] = fma(p_i, s, v1[0]);
-    });
-    dev::block_sum<1>(v1, red);
-    if (threadIdx.x == 0) part_g[blockIdx.x] = v1[0];
-    if (!grid_barrier(st, nb)) break;
-    T g1[1];
-    grid_sum_all<1>(part_g, nb, g1);
-    const T gamma = g1[0];
-    if (!(gamma > T(0)) || !isfinite(gamma)) {
-      done = kDoneBreakdown;
-      break;
-    }
-    alpha = rho / gamma;
-    if (lead && it < hist_len) a.alpha_h[it] = alpha;
-    // phase 2: x += alpha p, r -= alpha w, z = D^-1 r, (r,z), (r,r) on test iterations
-    ++it;
-    const bool check = (it % kchk == 0) || it >= max_it;
-    T v2[2] = {T(0), T(0)};
-    VT* xv = reinterpret_cast<VT*>(a.x);
-    VT* rv = reinterpret_cast<VT*>(a.r);
-    VT* zv = reinterpret_cast<VT*>(a.z);
-    const VT* pv = reinterpret_cast<const VT*>(a.p);
-    const VT* wv = reinterpret_cast<const VT*>(a.w);
-    const VT* dv = reinterpret_cast<const VT*>(a.dinv);
-    for (int64_t i = tid; i < nv; i += stride) {
-      VT xx = xv[i], rr4 = rv[i], zz;
-      const VT pp = pv[i], ww = __ldcg(wv + i), dd = __ldg(dv + i);
-      T* xe = reinterpret_cast<T*>(&xx);
-      T* re = reinterpret_cast<T*>(&rr4);
-      T* ze = reinterpret_cast<T*>(&zz);
-      const T* pe = reinterpret_cast<const T*>(&pp);
-      const T* we = reinterpret_cast<const T*>(&ww);
-      const T* de = reinterpret_cast<const T*>(&dd);
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        xe[e] = fma(alpha, pe[e], xe[e]);
-        re[e] = fma(-alpha, we[e], re[e]);
-        ze[e] = de[e] * re[e];
-        v2[0] = fma(re[e], ze[e], v2[0]);
-        if (check) v2[1] = fma(re[e], re[e], v2[1]);
-      }
-      xv[i] = xx;
-      rv[i] = rr4;
-      zv[i] = zz;
-    }
-    if (lead) {
-      for (int64_t i = nv * E; i < n; ++i) {
-        a.x[i] = fma(alpha, a.p[i], a.x[i]);
-        const T ri = fma(-alpha, a.w[i], a.r[i]);
-        const T zi = a.dinv[i] * ri;
-        a.r[i] = ri;
-        a.z[i] = zi;
-        v2[0] = fma(ri, zi, v2[0]);
-        if (check) v2[1] = fma(ri, ri, v2[1]);
-      }
-    }
-    dev::block_sum<2>(v2, red);
-    if (threadIdx.x == 0) {
-      part_u[blockIdx.x] = v2[0];
-      part_u[nb + blockIdx.x] = v2[1];
-    }
-    if (!grid_barrier(st, nb)) break;
-    T g2[2];
-    grid_sum_all<2>(part_u, nb, g2);
-    const T rz = g2[0];
-    if (check) rr = g2[1];
-    if ((check && rr == T(0)) || rz == T(0))
-      done = kDoneConverged;
-    else if (check && sqrt(rr) <= tol)
-      done = kDoneConverged;
-    else if (it >= max_it)
-      done = kDoneNotConverged;
-    else if (!isfinite(rz) || (check && !isfinite(rr)))
-      done = kDoneBreakdown;
-    if (done) break;
-    beta = rz / rho;
-    rho = rz;
-    if (lead && it - 1 < hist_len) a.beta_h[it - 1] = beta;
-    // phase 3: p = z + beta p
-    VT* pw = reinterpret_cast<VT*>(a.p);
-    for (int64_t i = tid; i < nv; i += stride) {
-      VT pp = pw[i];
-      const VT zz = __ldcg(zv + i);
-      T* pe = reinterpret_cast<T*>(&pp);
-      const T* ze = reinterpret_cast<const T*>(&zz);
-#pragma unroll
-      for (int e = 0; e < E; ++e) pe[e] = fma(beta, pe[e], ze[e]);
-      pw[i] = pp;
-    }
-    if (lead)
-      for (int64_t i = nv * E; i < n; ++i) a.p[i] = fma(beta, a.p[i], a.z[i]);
-    if (!grid_barrier(st, nb)) break;
-  }
-  if (lead) {
-    st->iter = it;
-    st->rho = rho;
-    st->rr = rr;
-    st->alpha = alpha;
-    st->beta = beta;
-    st->done = st->bar_err ? kDoneBreakdown : done;
-  }
-}
-
 template <class K>
 int occupancy_grid(K kernel, int sms, int64_t want) {
   int per_sm = 0;
@@ -596,27 +406,6 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
     c.grid_spmv = occupancy_grid(c.A.long_rows ? (void*)k1_kernel<false, true, T> : (void*)k1_kernel<false, false, T>,
                                  sms, spmv_blocks);
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
-}
-
-template <class T>
-int core_grid_blocks(const CgCore<T>& c, int sms) {
-  if (c.S.n > 0) return 0;  // the one-launch form reads the sliced-ELL copy
-  int per_sm = 0;
-  const void* k = c.A.long_rows ? (const void*)grid_cg_kernel<true, T> : (const void*)grid_cg_kernel<false, T>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0) != cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    return 0;
-  }
-  return std::min(per_sm * sms, dev::kMaxPartials / 3);
-}
-
-template <class T>
-apcg_status core_grid_solve(const CgCore<T>& c, T* x, cudaStream_t s, int nblocks) {
-  Args<T> a = make_args(c, x);
-  void* params[] = {&a};
-  const void* k = c.A.long_rows ? (const void*)grid_cg_kernel<true, T> : (const void*)grid_cg_kernel<false, T>;
-  APCG_CUDA(cudaLaunchCooperativeKernel(k, dim3((unsigned)nblocks), dim3(kThreads), params, 0, s));
-  return APCG_OK;
 }
 
 template <class T>
@@ -714,10 +503,6 @@ apcg_status core_setup_f64(const CgCore<double>& c, const double* b, double* x, 
 
 template void core_configure<double>(CgCore<double>&, int64_t, int);
 template void core_configure<float>(CgCore<float>&, int64_t, int);
-template int core_grid_blocks<double>(const CgCore<double>&, int);
-template int core_grid_blocks<float>(const CgCore<float>&, int);
-template apcg_status core_grid_solve<double>(const CgCore<double>&, double*, cudaStream_t, int);
-template apcg_status core_grid_solve<float>(const CgCore<float>&, float*, cudaStream_t, int);
 template apcg_status core_k1<double>(const CgCore<double>&, double*, cudaStream_t, bool);
 template apcg_status core_k1<float>(const CgCore<float>&, float*, cudaStream_t, bool);
 template apcg_status core_k2<double>(const CgCore<double>&, double*, cudaStream_t, bool, double,

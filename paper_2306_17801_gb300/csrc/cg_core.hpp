@@ -43,15 +43,6 @@ struct CgCore {
 template <class T>
 void core_configure(CgCore<T>& c, int64_t nnz, int sms);
 
-// The one-launch form: the whole iteration loop in one cooperative launch
-// (after the set-up kernel).  core_grid_blocks gives its grid (0: not
-// available for this core); the loop leaves the state block as the graph
-// form does (st->bar_err set if a bounded barrier wait ran out).
-template <class T>
-int core_grid_blocks(const CgCore<T>& c, int sms);
-template <class T>
-apcg_status core_grid_solve(const CgCore<T>& c, T* x, cudaStream_t s, int nblocks);
-
 // K1: w = A p, gamma = (p,w); the last block forms alpha (device mode) or only gamma (host mode).
 template <class T>
 apcg_status core_k1(const CgCore<T>& c, T* x, cudaStream_t s, bool host);

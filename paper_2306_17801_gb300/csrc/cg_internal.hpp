@@ -28,10 +28,6 @@ struct CgState {
   int32_t body_runs;   // executions of the graph body
   unsigned int ticket; // grid-reduction arrival counter
   int32_t pad;
-  // grid-wide barrier of the one-launch (cooperative) form
-  unsigned int bar_count, bar_gen;
-  int32_t bar_err;     // a bounded barrier wait ran out
-  int32_t pad2;
 };
 
 // Launch the A0 kernel dinv = 1 / diag(A) (flags bad diagonals on ctx).

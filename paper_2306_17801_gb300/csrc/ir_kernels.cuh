@@ -98,8 +98,6 @@ __device__ __forceinline__ void residual_body(const ResidualArgs& a, Spmv spmv) 
     st->hist_len = 0;
     st->body_runs = 0;
     st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
-    st->bar_count = 0;
-    st->bar_err = 0;
     st->done = (sqrtf(t32[1]) <= tol) ? kDoneConverged : 0;
   }
 }

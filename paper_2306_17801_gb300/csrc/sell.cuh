@@ -32,21 +32,12 @@ struct SellView {
   int32_t long_rows = 0;  // mean slice width >= 8: the kernels take the grouped path
 };
 
-// Loads of x: through the read-only path, valid when x does not change during
-// the kernel (COHERENT = false), or through the ordinary coherent path, for
-// kernels that rewrite x between grid-wide barriers (COHERENT = true).
-template <bool COHERENT, class T>
-__device__ __forceinline__ T ld_x(const T* p) {
-  if (COHERENT) return __ldca(p);
-  return ld_ro(p);
-}
-
 // Apply epi(row, (A x)[row], x[row]) for every row; warps of the grid take
 // slices in a grid-stride loop.  Values TV are widened to T, the type of x
 // and of the row sums.  All 32 lanes must call this function together.
 // LONG selects the grouped path for long rows (it needs more registers, so
 // short-row matrices use a separate instance).
-template <bool OWN_X, bool LONG, class T, bool COHERENT = false, class TV, class Epi>
+template <bool OWN_X, bool LONG, class T, class TV, class Epi>
 __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __restrict__ x, Epi epi) {
   constexpr int G = 8;  // entries per lane loaded before their FMAs (long rows)
   const int lane = threadIdx.x & 31;
@@ -65,7 +56,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
     }
     const int32_t row = (int32_t)(s * 32 + lane);
     T x_own = T(0);
-    if (OWN_X && row < A.n) x_own = ld_x<COHERENT>(x + row);
+    if (OWN_X && row < A.n) x_own = ld_ro(x + row);
     const int32_t* cp = A.col + base + lane;
     const TV* vp = A.val + base + lane;
     const int32_t width = (end - base) >> 5;
@@ -87,7 +78,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
           a[g] = ok ? ld_stream(vp + 32 * (k + g)) : TV(0);
         }
 #pragma unroll
-        for (int g = 0; g < G; ++g) xv[g] = (k + g < width) ? ld_x<COHERENT>(x + j[g]) : T(0);
+        for (int g = 0; g < G; ++g) xv[g] = (k + g < width) ? ld_ro(x + j[g]) : T(0);
 #pragma unroll
         for (int g = 0; g < G; ++g)
           if (k + g < width) acc = fma((T)a[g], xv[g], acc);
@@ -98,7 +89,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
       for (int32_t k = 0; k < width; ++k) {
         const int32_t j = ld_stream(cp + 32 * k);
         const TV a = ld_stream(vp + 32 * k);
-        acc = fma((T)a, ld_x<COHERENT>(x + j), acc);
+        acc = fma((T)a, ld_ro(x + j), acc);
       }
     }
     if (row < A.n) epi(row, acc, x_own);
