@@ -426,6 +426,9 @@ def small_case(apcg, ctx, dev):
         apcg.call("apcg_cg_plan_destroy", V(pl))
     out["speedup_async_graph_vs_host_sync"] = out["host_sync"]["us_per_iteration"] / out["async_graph"]["us_per_iteration"]
     out["speedup_persistent_vs_host_sync"] = out["host_sync"]["us_per_iteration"] / out["persistent"]["us_per_iteration"]
+    # fixed costs that bound a latency-bound iteration (a host-synchronous iteration pays two or three
+    # round trips, a graph iteration three dependent kernel launches)
+    out["launch_floor"] = apcg.launch_floor(ctx, 200)
     for h in (vb, vx):
         apcg.call("apcg_vec_destroy", V(h))
     apcg.call("apcg_mat_destroy", V(A))
@@ -816,7 +819,8 @@ def bench_stencil(args):
 
 def bench_tfqmr(args):
     """Jacobi-TFQMR (Sec. 4.3) on the 64^2 5-point and 128^3 7-point systems: host-synchronous vs
-    asynchronous forms, microseconds per iteration (two SpMVs each)."""
+    asynchronous forms (and the one-launch cluster form on the small system), microseconds per
+    iteration (two SpMVs each)."""
     import ctypes as C
 
     import torch
@@ -834,7 +838,8 @@ def bench_tfqmr(args):
         p = single_problem(cfg, seed=0)
         g = _gpu_problem(p, dev)
         row = {"n": p.n, "nnz": p.nnz, "k": k}
-        for mode in ("host_sync", "async", "async_graph"):
+        modes = ("host_sync", "async", "async_graph") + (("persistent",) if p.n <= 16384 else ())
+        for mode in modes:
             plan = apcg.tfqmr_plan_create(ctx, g["A"], apcg.cg_opts(rtol=1e-8, check_every=k, mode=mode, max_it=20000))
             best, r = None, None
             for i in range(max(2, args.steps // 3) + 1):
@@ -850,6 +855,8 @@ def bench_tfqmr(args):
             row[mode] = {"ms_per_solve": 1e3 * best, "iters": r["iters"], "us_per_iteration": 1e6 * best / r["iters"],
                          "kernel_launches": r["kernel_launches"]}
         row["speedup_async_graph_vs_host_sync"] = row["host_sync"]["ms_per_solve"] / row["async_graph"]["ms_per_solve"]
+        if "persistent" in row:
+            row["speedup_persistent_vs_host_sync"] = row["host_sync"]["ms_per_solve"] / row["persistent"]["ms_per_solve"]
         b_it = 24 * p.nnz + 8 * (p.n + 1) + 232 * p.n
         row["algorithmic_bytes_per_iteration"] = b_it
         row["GBps_per_iteration"] = b_it / (1e-6 * row["async_graph"]["us_per_iteration"]) / 1e9

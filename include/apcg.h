@@ -588,8 +588,12 @@ APCG_API apcg_status apcg_ir_plan_create_stencil(apcg_ctx ctx, apcg_stencil sten
  * b, x: device float64 [n], 16-byte aligned; x holds x0 on entry and the
  * iterate on exit.  Marks A and b read, x read-write.
  *
- * opts (apcg_cg_opts): rtol, atol, max_it (<= 0: 10 n), check_every k, mode
- * (HOST_SYNC, ASYNC; ASYNC_GRAPH for AUTO/PERSISTENT/ASYNC_GRAPH), history.
+ * opts (apcg_cg_opts): rtol, atol, max_it (<= 0: 10 n), check_every k, mode,
+ * history.  Modes: HOST_SYNC, ASYNC, ASYNC_GRAPH as for CG; PERSISTENT runs
+ * the whole solve in one thread-block-cluster launch and takes n <= 16384
+ * (APCG_ERR_UNSUPPORTED above that, or where the device cannot schedule the
+ * cluster); AUTO selects PERSISTENT where it applies, else ASYNC_GRAPH.  The
+ * persistent form reads the CSR arrays in place for the whole solve.
  * Convergence test, every k iterations and at max_it: Freund's bound
  * sqrt(2i + 1) tau_i <= max(rtol ||D^-1 b||, atol), tau_i the quasi-residual
  * norm after iteration i (two half-steps); a quasi-residual of exactly zero
@@ -681,6 +685,19 @@ APCG_API apcg_status apcg_cg_solve_batched(apcg_ctx ctx, int32_t nsys, const int
                                            const int32_t* rowptr, const int32_t* col, const double* val,
                                            const double* b, double* x, const apcg_cg_opts* opts,
                                            apcg_batch_result* results);
+
+/* ------------------------------------------------------------------ measurement support */
+
+/*
+ * Launch floors on ctx's stream (the paper has no counterpart; the benchmark
+ * reports them beside the per-iteration times of latency-bound solves), each
+ * averaged over `reps` repetitions, in microseconds of host wall time:
+ * us[0] one empty kernel launched and waited for; us[1] a graph of three
+ * dependent empty kernels launched and waited for; us[2] an 8-byte
+ * device-to-host copy and wait; us[3] the three-kernel graph launched back to
+ * back (per graph, one wait at the end).  us: host [4].  Blocks.
+ */
+APCG_API apcg_status apcg_launch_floor(apcg_ctx ctx, int32_t reps, double* us);
 
 /* ------------------------------------------------------------------ host-only simulation of the marking rules */
 

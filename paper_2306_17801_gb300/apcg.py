@@ -228,6 +228,7 @@ PROTOS = {
     "apcg_expr_describe": [P, P, P, C.c_char_p, C.c_size_t],
     "apcg_expr_execute_async": [P, P, P],
     "apcg_vec_axpy_expr_async": [P, P, P, P],
+    "apcg_launch_floor": [P, i32, P],
     "apcg_stencil_create": [i32, i32, i32, i32, P, P, PP],
     "apcg_stencil_destroy": [P],
     "apcg_stencil_apply_async": [P, P, P, P],
@@ -496,6 +497,13 @@ def expr_describe(expr) -> dict:
     buf = C.create_string_buffer(8192)
     call("apcg_expr_describe", C.c_void_p(expr), C.byref(ni), C.byref(nl), buf, len(buf))
     return {"instructions": ni.value, "inputs": nl.value, "text": buf.value.decode()}
+
+
+def launch_floor(ctx, reps=200) -> dict:
+    us = (C.c_double * 4)()
+    call("apcg_launch_floor", C.c_void_p(ctx), int(reps), us)
+    return {"empty_kernel_sync_us": us[0], "graph3_sync_us": us[1], "d2h_8B_sync_us": us[2],
+            "graph3_back_to_back_us": us[3]}
 
 
 def stencil_create(dims, offsets, weights):

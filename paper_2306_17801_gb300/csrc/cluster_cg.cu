@@ -31,52 +31,16 @@ namespace {
 using clu::cgx::cluster_group;
 
 // Shared-memory bookkeeping common to both kernels; returns the Shared view.
-struct Block {
-  double slot[2][4];
-  double red[4 * kClusterThreads];
-  double tot[4];
-  double* peer_slot[clu::kMaxCluster];
-  void* peer_data[2][clu::kMaxCluster];  // the dynamic arrays of every CTA
-  int sys;
-};
-
-__device__ clu::Shared setup_block(Block& B, cluster_group& cl, void* dyn0, void* dyn1) {
-  const int C = (int)cl.num_blocks();
-  if (threadIdx.x < C) {
-    B.peer_slot[threadIdx.x] = cl.map_shared_rank(&B.slot[0][0], (unsigned)threadIdx.x);
-    B.peer_data[0][threadIdx.x] = cl.map_shared_rank(dyn0, (unsigned)threadIdx.x);
-    B.peer_data[1][threadIdx.x] = dyn1 ? cl.map_shared_rank(dyn1, (unsigned)threadIdx.x) : nullptr;
-  }
-  __syncthreads();
-  clu::Shared S;
-  S.slot = &B.slot[0][0];
-  S.peer_slot = B.peer_slot;
-  S.red = B.red;
-  S.tot = B.tot;
-  S.C = C;
-  S.rank = (int)cl.block_rank();
-  return S;
-}
-
-// Next system index of the cluster's work queue (uniform across the cluster).
-__device__ int next_system(Block& B, const ClusterArgs& a, cluster_group& cl, int rank) {
-  if (rank == 0 && threadIdx.x == 0) B.sys = (int)atomicAdd(a.next, 1u);
-  cl.sync();
-  const int idx = *cl.map_shared_rank(&B.sys, 0u);
-  cl.sync();  // every CTA has read the index before rank 0 may overwrite it or exit
-  return idx;
-}
-
 template <int R>
 __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(ClusterArgs a) {
   cluster_group cl = clu::cgx::this_cluster();
   extern __shared__ double s_p[];  // this CTA's slice of p
-  __shared__ Block B;
-  const clu::Shared S = setup_block(B, cl, s_p, nullptr);
+  __shared__ clu::Block B;
+  const clu::Shared S = clu::setup_block(B, cl, s_p, nullptr);
   double* const* peer_p = reinterpret_cast<double* const*>(B.peer_data[0]);
   int parity = 0;
   for (;;) {
-    const int idx = next_system(B, a, cl, S.rank);
+    const int idx = clu::next_system(B, a.next, cl, S.rank);
     if (idx >= a.nsys) break;
     const int s = a.order ? a.order[idx] : idx;
     const SysDesc d = a.sys[s];
@@ -166,13 +130,13 @@ __global__ void __launch_bounds__(kClusterThreads, (R >= 8 ? 1 : 2)) cg_cluster_
   extern __shared__ double s_dyn[];
   double* s_x = s_dyn;
   float* s_p = reinterpret_cast<float*>(s_dyn + rpc_max);
-  __shared__ Block B;
-  const clu::Shared S = setup_block(B, cl, s_x, s_p);
+  __shared__ clu::Block B;
+  const clu::Shared S = clu::setup_block(B, cl, s_x, s_p);
   double* const* peer_x = reinterpret_cast<double* const*>(B.peer_data[0]);
   float* const* peer_p = reinterpret_cast<float* const*>(B.peer_data[1]);
   int parity = 0;
   for (;;) {
-    const int idx = next_system(B, a, cl, S.rank);
+    const int idx = clu::next_system(B, a.next, cl, S.rank);
     if (idx >= a.nsys) break;
     const int s = a.order ? a.order[idx] : idx;
     const SysDesc d = a.sys[s];

@@ -68,4 +68,11 @@ cudaError_t launch_cluster_cg(const ClusterArgs& args, const ClusterShape& sh, i
 // Clusters of this shape that fit on the device at once (0: not schedulable).
 int max_active_clusters(const ClusterShape& sh);
 
+// Whole-solve Jacobi-TFQMR (cluster_tfqmr.cu): the launch shape for systems of
+// up to n rows (ok = false above 16384 rows or if none is schedulable), and
+// the launch (args as for CG; res receives iters, done, the squared bound as
+// rr and ||D^-1 b||^2 as bnorm2).
+ClusterShape tfqmr_cluster_shape(int n);
+cudaError_t launch_cluster_tfqmr(const ClusterArgs& args, const ClusterShape& sh, int nclusters, cudaStream_t s);
+
 }  // namespace apcg

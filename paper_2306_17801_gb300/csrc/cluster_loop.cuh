@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #include "cg_internal.hpp"
+#include "cluster_cg.hpp"
 #include "kernels_common.cuh"
 
 namespace apcg {
@@ -63,6 +64,44 @@ __device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& pa
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = (T)S.tot[k];
   parity ^= 1;
+}
+
+// Per-CTA bookkeeping of a whole-solve cluster kernel (static shared memory).
+struct Block {
+  double slot[2][4];
+  double red[4 * kClusterThreads];
+  double tot[4];
+  double* peer_slot[kMaxCluster];
+  void* peer_data[2][kMaxCluster];  // the dynamic arrays of every CTA
+  int sys;
+};
+
+// Map the cluster's shared arrays (slots and up to two dynamic arrays per CTA).
+__device__ __forceinline__ Shared setup_block(Block& B, cgx::cluster_group& cl, void* dyn0, void* dyn1) {
+  const int C = (int)cl.num_blocks();
+  if (threadIdx.x < C) {
+    B.peer_slot[threadIdx.x] = cl.map_shared_rank(&B.slot[0][0], (unsigned)threadIdx.x);
+    B.peer_data[0][threadIdx.x] = cl.map_shared_rank(dyn0, (unsigned)threadIdx.x);
+    B.peer_data[1][threadIdx.x] = dyn1 ? cl.map_shared_rank(dyn1, (unsigned)threadIdx.x) : nullptr;
+  }
+  __syncthreads();
+  Shared S;
+  S.slot = &B.slot[0][0];
+  S.peer_slot = B.peer_slot;
+  S.red = B.red;
+  S.tot = B.tot;
+  S.C = C;
+  S.rank = (int)cl.block_rank();
+  return S;
+}
+
+// Next system index of the cluster's work queue (uniform across the cluster).
+__device__ __forceinline__ int next_system(Block& B, unsigned int* next, cgx::cluster_group& cl, int rank) {
+  if (rank == 0 && threadIdx.x == 0) B.sys = (int)atomicAdd(next, 1u);
+  cl.sync();
+  const int idx = *cl.map_shared_rank(&B.sys, 0u);
+  cl.sync();  // every CTA has read the index before rank 0 may overwrite it or exit
+  return idx;
 }
 
 // Geometry of the CTA's rows in the current system.

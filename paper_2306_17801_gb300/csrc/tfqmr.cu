@@ -30,7 +30,10 @@
 // CG (Sec. 4.3).  The solve modes are those of the CG plan: HOST_SYNC (every
 // reduction read by the host, scalars passed by value), ASYNC (host reads the
 // done word every k iterations) and ASYNC_GRAPH (k iterations in the body of
-// a conditional while node).  AUTO and PERSISTENT select ASYNC_GRAPH.
+// a conditional while node), and PERSISTENT: the whole solve in one
+// thread-block-cluster launch (cluster_tfqmr.cu) for systems of at most
+// 16384 rows, with the CSR matrix read in place.  AUTO selects PERSISTENT
+// where that kernel fits and ASYNC_GRAPH otherwise.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -40,6 +43,7 @@
 
 #include "apcg_internal.hpp"
 #include "cg_internal.hpp"
+#include "cluster_cg.hpp"
 #include "kernels_common.cuh"
 #include "sell.cuh"
 #include "sell.hpp"
@@ -48,6 +52,7 @@ namespace apcg {
 namespace tq {
 
 constexpr int kThreads = 256;
+constexpr int kClusterMaxRows = 16384;  // the whole-solve cluster kernel: 16 CTAs x 512 threads x 2 rows
 
 // Device-resident scalars of one TFQMR solve.
 struct TqState {
@@ -403,6 +408,12 @@ struct apcg_tfqmr_plan_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double* graph_x = nullptr;
+  // whole-solve cluster mode (small systems, cluster_tfqmr.cu)
+  apcg::ClusterShape shape;
+  apcg::SysDesc* sys = nullptr;
+  apcg::SysResult* sres = nullptr;
+  unsigned int* next = nullptr;
+  apcg::SysResult* sres_host = nullptr;
 };
 
 namespace apcg {
@@ -669,6 +680,36 @@ apcg_status enqueue_async(Plan P, const double* b, double* x, bool graph) {
   return APCG_OK;
 }
 
+// The whole solve in one cluster launch (small systems).
+apcg_status enqueue_persistent(Plan P, const double* b, double* x) {
+  cudaStream_t s = P->ctx->stream;
+  ClusterArgs ca{};
+  ca.rowptr = P->A.rowptr;
+  ca.col = P->A.col;
+  ca.val = static_cast<const double*>(P->A.val);
+  ca.b = b;
+  ca.x = x;
+  ca.sys = P->sys;
+  ca.nsys = 1;
+  ca.check_every = P->k;
+  ca.next = P->next;
+  ca.res = P->sres;
+  ca.rtol = P->opts.rtol;
+  ca.atol = P->opts.atol;
+  ca.max_it = P->max_it;
+  ca.hist_len = P->hist_len;
+  ca.alpha_h = P->a.alpha_h;
+  ca.beta_h = P->a.beta_h;
+  APCG_CUDA(cudaMemsetAsync(P->next, 0, sizeof(unsigned int), s));
+  APCG_CUDA(launch_cluster_tfqmr(ca, P->shape, 1, s));
+  count_kernels(1);
+  P->last_launches = 1;
+  APCG_CUDA(cudaMemcpyAsync(P->sres_host, P->sres, sizeof(SysResult), cudaMemcpyDeviceToHost, s));
+  counters().d2h_copies++;
+  counters().d2h_bytes += sizeof(SysResult);
+  return APCG_OK;
+}
+
 apcg_status finish_async(Plan P) {
   APCG_CUDA(cudaStreamSynchronize(P->ctx->stream));
   counters().host_syncs++;
@@ -688,6 +729,19 @@ apcg_status finish_async(Plan P) {
 }
 
 void fill_result(Plan P, apcg_cg_result* res) {
+  if (P->mode == APCG_MODE_PERSISTENT) {
+    const SysResult& r = *P->sres_host;
+    res->iters = r.iters;
+    res->reason = r.done == kDoneConverged      ? APCG_CONVERGED
+                  : r.done == kDoneBreakdown    ? APCG_BREAKDOWN
+                  : r.done == kDoneBadDiagonal ? APCG_BAD_DIAGONAL
+                                                : APCG_NOT_CONVERGED;
+    res->rr = r.rr;
+    res->bnorm = std::sqrt(r.bnorm2);
+    res->rel_res = res->bnorm > 0.0 ? std::sqrt(r.rr) / res->bnorm : std::sqrt(r.rr);
+    res->kernel_launches = P->last_launches;
+    return;
+  }
   const TqState* h = P->st_host;
   res->iters = h->iter;
   res->reason = h->done == kDoneConverged ? APCG_CONVERGED
@@ -711,9 +765,10 @@ apcg_status plan_destroy(Plan P) {
     }
     cudaFreeAsync(P->ws, P->ctx->stream);
   }
-  if (P->st_host) {
-    cudaStreamSynchronize(P->ctx->stream);  // the pinned mirror may be the target of an enqueued copy
-    cudaFreeHost(P->st_host);
+  if (P->st_host || P->sres_host) {
+    cudaStreamSynchronize(P->ctx->stream);  // the pinned mirrors may be the target of an enqueued copy
+    if (P->st_host) cudaFreeHost(P->st_host);
+    if (P->sres_host) cudaFreeHost(P->sres_host);
   }
   delete P;
   return APCG_OK;
@@ -737,8 +792,17 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   P->max_it = o.max_it > 0 ? o.max_it : (P->n > 0 ? 10 * P->n : 10);
   P->hist_len = o.history_len;
   P->mode = (o.mode == APCG_MODE_HOST_SYNC || o.mode == APCG_MODE_ASYNC) ? o.mode : APCG_MODE_ASYNC_GRAPH;
+  if (o.mode == APCG_MODE_PERSISTENT || o.mode == APCG_MODE_AUTO) {
+    P->shape = P->n <= kClusterMaxRows ? tfqmr_cluster_shape(P->n) : ClusterShape{};
+    if (P->n > kClusterMaxRows) P->shape.ok = false;
+    if (P->shape.ok)
+      P->mode = APCG_MODE_PERSISTENT;
+    else if (o.mode == APCG_MODE_PERSISTENT)
+      return set_error(APCG_ERR_UNSUPPORTED, "persistent TFQMR handles at most %d rows (got %d)", kClusterMaxRows,
+                       P->n);
+  }
   SellLayout L;
-  APCG_TRY(sell_layout(ctx->stream, P->n, A->rowptr, &L));
+  if (P->mode != APCG_MODE_PERSISTENT) APCG_TRY(sell_layout(ctx->stream, P->n, A->rowptr, &L));
   const int sms = ctx_num_sms(ctx);
   P->long_rows = L.long_rows != 0;
   const int64_t slices = ((int64_t)P->n + 31) / 32;
@@ -754,7 +818,8 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   const size_t nsptr = up(sizeof(int32_t) * ((size_t)L.nslices + 1));
   const size_t ncol = up(sizeof(int32_t) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nval = up(sizeof(double) * (size_t)std::max<int64_t>(L.padded, 1));
-  const size_t total = 9 * nv + npart + nst + 2 * nh + nsptr + ncol + nval;
+  const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
+  const size_t total = 9 * nv + npart + nst + 2 * nh + nsptr + ncol + nval + nsysb;
   char* ws = nullptr;
   APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
   P->ws = ws;
@@ -781,10 +846,22 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   int32_t* sptr = reinterpret_cast<int32_t*>(q);
   int32_t* scol = reinterpret_cast<int32_t*>(q + nsptr);
   double* sval = reinterpret_cast<double*>(q + nsptr + ncol);
-  APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice, ctx->stream));
-  counters().h2d_copies++;
-  APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val), scol,
-                                     sval));
+  if (P->mode != APCG_MODE_PERSISTENT) {
+    APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice,
+                              ctx->stream));
+    counters().h2d_copies++;
+    APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
+                                       scol, sval));
+  }
+  char* tail = q + nsptr + ncol + nval;
+  P->sys = reinterpret_cast<SysDesc*>(tail);
+  P->sres = reinterpret_cast<SysResult*>(tail + sizeof(SysDesc));
+  P->next = reinterpret_cast<unsigned int*>(tail + sizeof(SysDesc) + sizeof(SysResult));
+  SysDesc d0{};
+  d0.row0 = 0;
+  d0.n = P->n;
+  APCG_CUDA(cudaMemcpyAsync(P->sys, &d0, sizeof(d0), cudaMemcpyHostToDevice, ctx->stream));
+  APCG_CUDA(cudaMallocHost((void**)&P->sres_host, sizeof(SysResult)));
   a.A.n = P->n;
   a.A.nslices = L.nslices;
   a.A.sptr = sptr;
@@ -843,8 +920,9 @@ apcg_status apcg_tfqmr_plan_solve(apcg_tfqmr_plan P, apcg_vec b, apcg_vec x, apc
   OpScope op(P->ctx);
   op.read(P->A.id).read(b->id).rw(x->id).rw(P->id);
   APCG_TRY(op.begin());
-  apcg_status st = P->mode == APCG_MODE_HOST_SYNC ? tq::solve_host_sync(P, bp, xp)
-                                                  : tq::enqueue_async(P, bp, xp, P->mode == APCG_MODE_ASYNC_GRAPH);
+  apcg_status st = P->mode == APCG_MODE_HOST_SYNC    ? tq::solve_host_sync(P, bp, xp)
+                   : P->mode == APCG_MODE_PERSISTENT ? tq::enqueue_persistent(P, bp, xp)
+                                                     : tq::enqueue_async(P, bp, xp, P->mode == APCG_MODE_ASYNC_GRAPH);
   apcg_status st2 = op.finish();
   APCG_TRY(st);
   APCG_TRY(st2);

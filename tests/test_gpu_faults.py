@@ -81,7 +81,7 @@ def test_cg_reports_breakdown_on_non_finite_input(ctx, mode, where):
     assert ok["reason"] == "converged"
 
 
-@pytest.mark.parametrize("mode", ["host_sync", "async_graph"])
+@pytest.mark.parametrize("mode", ["host_sync", "async_graph", "persistent"])
 def test_tfqmr_reports_breakdown_on_nan(ctx, mode):
     A, b = _system()
     b = b.copy()

@@ -234,3 +234,11 @@ def test_mixed_api_cg_listing(dev):
         apcg.call("apcg_vec_destroy", V(v))
     apcg.call("apcg_mat_destroy", V(A))
     _destroy(ca, cb, cc)
+
+
+def test_launch_floor_reports_positive_times(dev):
+    ctx = apcg.ctx_create()
+    f = apcg.launch_floor(ctx, 20)
+    assert all(0.0 < v < 1e5 for v in f.values()), f
+    assert f["graph3_back_to_back_us"] <= f["graph3_sync_us"] * 1.5
+    apcg.call("apcg_ctx_destroy", C.c_void_p(ctx))

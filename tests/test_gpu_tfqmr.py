@@ -13,7 +13,9 @@ high-contrast systems (S reaches 1e-10 within 10 iterations on the 27-point
 variable-coefficient system, against 1e-15 for CG), so a fixed 1e-12 bar
 would test the conditioning of the method rather than the implementation.
 The GPU also forms M u as M w + beta M u2 (linearity) where the oracle
-applies M to u; the two differ only in rounding.
+applies M to u; the two differ only in rounding.  The persistent mode (the
+whole solve in one thread-block-cluster launch, systems of at most 16384
+rows) is held to the same bars as the three multi-kernel modes.
 """
 
 import ctypes as C
@@ -37,7 +39,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2306_17801_gb300 import apcg  # noqa: E402
 
-MODES = ["host_sync", "async", "async_graph"]
+MODES = ["host_sync", "async", "async_graph", "persistent"]
 
 
 @pytest.fixture(scope="module")
@@ -195,11 +197,28 @@ def test_tfqmr_plan_reuse_and_async_graph_syncs(ctx):
         apcg.call(fn, C.c_void_p(h))
 
 
+def test_tfqmr_persistent_selection(ctx):
+    # AUTO runs a small system in one launch, and the result equals that of an explicit PERSISTENT plan
+    A, b = SYSTEMS["convdiff"]
+    ra, xa = _solve(ctx, A, b, rtol=1e-8, check_every=3, mode="auto")
+    rp, xp = _solve(ctx, A, b, rtol=1e-8, check_every=3, mode="persistent")
+    assert ra["kernel_launches"] == rp["kernel_launches"] == 1
+    assert ra["iters"] == rp["iters"] and np.array_equal(xa, xp)
+    # above 16384 rows AUTO falls back to the graph form and PERSISTENT is refused
+    big = laplace_2d_5pt(130, shift=0.1)
+    bb = rhs_from_solution(big, np.random.default_rng(5).uniform(-1, 1, big.n))
+    r, _ = _solve(ctx, big, bb, rtol=1e-6, check_every=10, mode="auto")
+    assert r["reason"] == "converged" and r["kernel_launches"] > 1
+    with pytest.raises(apcg.ApcgError):
+        _solve(ctx, big, bb, mode="persistent")
+
+
 @pytest.mark.parametrize("cfg", ["c1", "c2"])
 def test_tfqmr_full_size(ctx, cfg):
     """The benchmark systems (64^2 5-point, 128^3 7-point) at rtol 1e-8."""
     p = single_problem(cfg, seed=0)
     k = 1 if cfg == "c1" else 10
     ref = oracle.tfqmr(p.A, p.b, rtol=1e-8, check_every=k, hist_len=10)
-    res, x = _solve(ctx, p.A, p.b, rtol=1e-8, check_every=k, mode="async_graph", max_it=20000)
-    _check(res, x, ref, k, A=p.A, b=p.b)
+    for mode in ("async_graph", "persistent") if p.n <= 16384 else ("async_graph",):
+        res, x = _solve(ctx, p.A, p.b, rtol=1e-8, check_every=k, mode=mode, max_it=20000)
+        _check(res, x, ref, k, A=p.A, b=p.b)
