@@ -51,9 +51,27 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def _code_tokens(text: bytes) -> bytes:
+    """Source text without comments and with whitespace runs collapsed (string literals kept)."""
+    import re
+
+    tok = re.compile(rb'"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|//[^\n]*|/\*.*?\*/|\s+', re.S)
+
+    def keep(m):
+        t = m.group(0)
+        if t.startswith(b"//") or t.startswith(b"/*"):
+            return b" "
+        if t[:1].isspace():
+            return b" "
+        return t
+
+    return re.sub(rb" +", b" ", tok.sub(keep, text)).strip()
+
+
 def unit_hash(unit: str) -> str:
-    """sha256 over one translation unit and every local header it includes, transitively
-    (identifies the build of the kernels defined in that unit)."""
+    """sha256 over one translation unit and every local header it includes, transitively,
+    with comments and layout removed (identifies the code of the kernels defined in that
+    unit: an edit of a comment keeps the hash)."""
     import hashlib
     import re
 
@@ -76,7 +94,7 @@ def unit_hash(unit: str) -> str:
     h = hashlib.sha256()
     for p in sorted(seen):
         h.update(os.path.basename(p).encode())
-        h.update(seen[p])
+        h.update(_code_tokens(seen[p]))
     return h.hexdigest()[:16]
 
 
