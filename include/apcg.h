@@ -249,8 +249,14 @@ APCG_API apcg_status apcg_vec_destroy(apcg_vec v);
  * Non-owning view of a square or rectangular CSR matrix (AIJ, Sec. 4.1) in
  * device memory: rowptr[nrows+1] (int32, rowptr[0] = 0, non-decreasing),
  * col[nnz] (int32 in [0, ncols)), val[nnz] of `dtype`.  Column indices
- * need not be sorted, but the row sums are formed in storage order.  The
- * structure is not checked on the device unless apcg_mat_validate is called.
+ * need not be sorted, but the row sums are formed in storage order.
+ * Wrapping checks nothing on the device.  The CG, TFQMR and refinement plans
+ * check the structure when they are created (rowptr copied back: starts at
+ * 0, never decreases, ends at nnz; column indices in [0, ncols) by a device
+ * pass) and return APCG_ERR_INVALID_ARG before any kernel reads through it.
+ * The asynchronous operations (apcg_mat_mult_async, apcg_pc_jacobi_setup_async)
+ * and the batched plans, which take raw CSR arrays, trust the structure:
+ * call apcg_mat_validate first where it may be malformed.
  */
 APCG_API apcg_status apcg_mat_csr_wrap(const int32_t* rowptr, const int32_t* col, const void* val, int32_t nrows,
                               int32_t ncols, int64_t nnz, apcg_dtype dtype, apcg_mat* out);

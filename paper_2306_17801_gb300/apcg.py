@@ -278,11 +278,21 @@ def last_error() -> str:
     return load().apcg_last_error_string().decode()
 
 
+# Tensors behind the views made by vec_wrap / mat_wrap, by handle: the library keeps raw device pointers, so
+# the binding keeps the tensors alive until the view is destroyed (a view of freed memory would let the
+# caching allocator hand the same bytes to the next tensor).
+_views: dict[int, tuple] = {}
+_DESTROY = {"apcg_vec_destroy", "apcg_mat_destroy"}
+
+
 def call(name: str, *args):
     """Call an entry point; raise ApcgError on a non-zero status."""
     st = getattr(load(), name)(*args)
     if st != OK:
         raise ApcgError(st, last_error())
+    if name in _DESTROY and args:
+        h = args[0]
+        _views.pop(h.value if isinstance(h, C.c_void_p) else h, None)
     return st
 
 
@@ -375,6 +385,7 @@ def vec_wrap(t, dtype=None):
             raise ValueError(f"unsupported dtype {t.dtype}")
     h = _out()
     call("apcg_vec_wrap", C.c_void_p(_ptr(t) if t.numel() else 0), t.numel(), dtype, C.byref(h))
+    _views[h.value] = (t,)
     return h.value
 
 
@@ -402,6 +413,7 @@ def mat_wrap(rowptr, col, val, ncols=None):
         dtype,
         C.byref(h),
     )
+    _views[h.value] = (rowptr, col, val)
     return h.value
 
 

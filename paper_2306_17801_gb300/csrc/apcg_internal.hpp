@@ -51,7 +51,7 @@ Counters& counters();
 constexpr int kEventRing = 128;
 
 // Device-side error word of a context: kernels OR flags into it.
-enum : int32_t { kDevErrBadDiagonal = 1, kDevErrNonFinite = 2, kDevErrTimeout = 4 };
+enum : int32_t { kDevErrBadDiagonal = 1, kDevErrNonFinite = 2, kDevErrTimeout = 4, kDevErrBadIndex = 8 };
 
 struct ReduceScratch {
   double* partials = nullptr;  // [kMaxPartials * 3]

@@ -306,7 +306,9 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
   // The iteration kernels read a sliced-ELL copy of A (sell.cuh); the cluster kernel reads the CSR itself.
   SellLayout L;
   const bool need_sell = A && P->mode != APCG_MODE_PERSISTENT;
-  if (need_sell) APCG_TRY(sell_layout(ctx->stream, c.n, A->rowptr, &L));
+  std::vector<int32_t> rp;
+  if (A) APCG_TRY(csr_check(ctx, A, &rp));
+  if (need_sell) APCG_TRY(sell_layout_host(c.n, rp, &L));
   // Workspace: dinv, r, p, w, z, partials, state, histories, cluster bookkeeping (one stream-ordered block).
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(double) * (size_t)(c.n > 0 ? c.n : 1));

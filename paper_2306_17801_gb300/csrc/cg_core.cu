@@ -163,13 +163,13 @@ __device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma) {
   }
 }
 
-// K1
-template <bool HOST, bool LONG, class T>
+// K1 (G: group size of the long-row path)
+template <bool HOST, bool LONG, class T, int G = 8>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   if (!HOST && read_done(a.st)) return;
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
-  dev::sell_spmv<true, LONG, T>(a.A, a.p, [&](int32_t i, T s, T p_i) {
+  dev::sell_spmv<true, LONG, T, G>(a.A, a.p, [&](int32_t i, T s, T p_i) {
                                      a.w[i] = s;
                                      v[0] = fma(p_i, s, v[0]);
                                    });
@@ -381,13 +381,24 @@ apcg_status k1_stencil_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream
   return APCG_OK;
 }
 
+// Groups of 9 in the float64 K1 only: the float32 inner solves are bound by HBM, not by wasted FMA slots,
+// and the larger groups cost them occupancy (refinement at 160^3: 110.2 against 107.3 ms).
+template <class T>
+constexpr bool kGroup9 = std::is_same<T, double>::value;
+
+// The K1 instance for the plan's layout (short rows, groups of 8, groups of 9).
+template <bool HOST, class T>
+void* k1_instance(const CgCore<T>& c) {
+  if constexpr (kGroup9<T>)
+    if (c.A.long_rows == 9) return (void*)k1_kernel<HOST, true, T, 9>;
+  return c.A.long_rows ? (void*)k1_kernel<HOST, true, T> : (void*)k1_kernel<HOST, false, T>;
+}
+
 template <bool HOST, class T>
 apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
   if (c.S.n > 0) return k1_stencil_dispatch<HOST>(c, a, s);
-  if (c.A.long_rows)
-    k1_kernel<HOST, true, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
-  else
-    k1_kernel<HOST, false, T><<<c.grid_spmv, kThreads, 0, s>>>(a);
+  void* args[] = {const_cast<Args<T>*>(&a)};
+  APCG_CUDA(cudaLaunchKernel(k1_instance<HOST>(c), dim3(c.grid_spmv), dim3(kThreads), args, 0, s));
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -403,8 +414,7 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
   if (c.S.n > 0)
     c.grid_spmv = occupancy_grid((void*)k1_stencil_kernel<false, 7, T>, sms, ((int64_t)c.n + kThreads - 1) / kThreads);
   else
-    c.grid_spmv = occupancy_grid(c.A.long_rows ? (void*)k1_kernel<false, true, T> : (void*)k1_kernel<false, false, T>,
-                                 sms, spmv_blocks);
+    c.grid_spmv = occupancy_grid(k1_instance<false>(c), sms, spmv_blocks);
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
 }
 

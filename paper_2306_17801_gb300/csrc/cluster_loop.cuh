@@ -38,14 +38,56 @@ struct Shared {
   int C, rank;
 };
 
-// Sum NV values over the cluster.  The CTA's block sums go to its slot, a
-// cluster barrier publishes them, and every CTA adds the C slots in rank
-// order with the same warp tree, so all threads of all CTAs get the same bits.
+// Sum NV values over the block with the adds spread over the SM's four
+// sub-partitions (the block sum of the cluster sums below, on the
+// latency-critical path of every iteration): each float64 warp instruction
+// holds its sub-partition's pipe for about 64 cycles whatever its number of
+// active lanes, so a chain of adds in one warp is slow.  Warps 0..3 (one per sub-partition) each add every fourth
+// group of 32 values and reduce by shuffles; warp 0 adds their four results.
+// The order is fixed, so the result is the same bits on every call.  Not used
+// in the grid kernels, where the extra code costs the SpMV a register.  The
+// result is valid in threads 0..31; smem must hold NV * blockDim.x values;
+// blockDim.x must be a multiple of 32.
+template <int NV, class T>
+__device__ __forceinline__ void block_sum_quad(T (&v)[NV], T* smem) {
+  __shared__ T s_q[NV * 4];
+  const int nt = blockDim.x;
+  const int nq = nt >= 128 ? 4 : nt >> 5;
+  __syncthreads();  // smem and s_q may still be read by a previous call
+#pragma unroll
+  for (int k = 0; k < NV; ++k) smem[k * nt + threadIdx.x] = v[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  if (q < nq) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      T t = smem[k * nt + threadIdx.x];
+      for (int i = threadIdx.x + 32 * nq; i < nt; i += 32 * nq) t += smem[k * nt + i];
+      t = dev::warp_sum(t);
+      if (lane == 0) s_q[k * 4 + q] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      T t = lane < nq ? s_q[k * 4 + lane] : T(0);
+      t += __shfl_down_sync(dev::kFull, t, 2);
+      t += __shfl_down_sync(dev::kFull, t, 1);
+      v[k] = t;
+    }
+  }
+}
+
+// Sum NV values over the cluster.  The CTA's block sums (block_sum_quad) go
+// to its slot, a cluster barrier publishes them, and every CTA adds the C
+// slots in rank order with the same warp tree, so all threads of all CTAs
+// get the same bits.
 // Slots alternate between two buffers: a buffer is rewritten only two sums
 // later, after a barrier that every CTA passes only once done reading it.
 template <int NV, class T>
 __device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& parity, cgx::cluster_group& cl) {
-  dev::block_sum<NV>(v, reinterpret_cast<T*>(S.red));
+  block_sum_quad<NV>(v, reinterpret_cast<T*>(S.red));
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) S.slot[parity * 4 + k] = (double)v[k];

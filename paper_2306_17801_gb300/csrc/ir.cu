@@ -174,7 +174,9 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   P->grid_res = c.grid_spmv;
   P->grid_upd = std::max(1, std::min(sms * 8, (int)((P->n / 4 + kThreads - 1) / kThreads)));
   SellLayout L;
-  APCG_TRY(sell_layout(ctx->stream, P->n, S.rowptr, &L));
+  std::vector<int32_t> rp;
+  APCG_TRY(csr_check(ctx, &S, &rp));
+  APCG_TRY(sell_layout_host(P->n, rp, &L));
   // Workspace: sliced-ELL (sptr, col, float32 values, float64 values if A64), dinv32, r, p, w, z, d,
   // partials and states.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };

@@ -266,6 +266,7 @@ apcg_status ctx_check_device_error(apcg_ctx ctx) {
   counters().d2h_bytes += sizeof(flag);
   if (!flag) return APCG_OK;
   APCG_CUDA(cudaMemsetAsync(ctx->scratch.dev_error, 0, sizeof(int32_t), ctx->stream));
+  if (flag & kDevErrBadIndex) return set_error(APCG_ERR_INVALID_ARG, "CSR: a column index is outside [0, ncols)");
   if (flag & kDevErrBadDiagonal)
     return set_error(APCG_ERR_BAD_DIAGONAL, "Jacobi: a diagonal entry is missing, zero or not finite");
   if (flag & kDevErrTimeout) return set_error(APCG_ERR_TIMEOUT, "a bounded device wait ran out");

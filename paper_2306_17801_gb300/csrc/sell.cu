@@ -39,13 +39,17 @@ __global__ void sell_fill_kernel(int32_t n, int32_t nslices, const int32_t* __re
 }  // namespace
 
 apcg_status sell_layout(cudaStream_t s, int32_t n, const int32_t* rowptr_dev, SellLayout* out) {
-  out->n = n;
-  out->nslices = (n + 31) / 32;
   std::vector<int32_t> rp((size_t)n + 1);
   APCG_CUDA(cudaMemcpyAsync(rp.data(), rowptr_dev, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, s));
   APCG_CUDA(cudaStreamSynchronize(s));
   counters().d2h_copies++;
   counters().d2h_bytes += (int64_t)(sizeof(int32_t) * rp.size());
+  return sell_layout_host(n, rp, out);
+}
+
+apcg_status sell_layout_host(int32_t n, const std::vector<int32_t>& rp, SellLayout* out) {
+  out->n = n;
+  out->nslices = (n + 31) / 32;
   out->sptr.assign((size_t)out->nslices + 1, 0);
   out->max_width = 0;
   int64_t acc = 0;
@@ -61,7 +65,17 @@ apcg_status sell_layout(cudaStream_t s, int32_t n, const int32_t* rowptr_dev, Se
   }
   out->sptr[out->nslices] = (int32_t)acc;
   out->padded = acc;
-  out->long_rows = out->nslices > 0 && acc >= 8LL * 32 * out->nslices;
+  out->long_rows = 0;
+  if (out->nslices > 0 && acc >= 8LL * 32 * out->nslices) {
+    // FMA slots issued per lane with groups of 8 and of 9 (whole groups per slice); fewer wins, 8 on a tie
+    int64_t slots8 = 0, slots9 = 0;
+    for (int32_t sl = 0; sl < out->nslices; ++sl) {
+      const int64_t w = (out->sptr[sl + 1] - out->sptr[sl]) / 32;
+      slots8 += (w + 7) / 8 * 8;
+      slots9 += (w + 8) / 9 * 9;
+    }
+    out->long_rows = slots9 < slots8 ? 9 : 8;
+  }
   return APCG_OK;
 }
 

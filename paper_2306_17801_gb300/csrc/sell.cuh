@@ -29,17 +29,21 @@ struct SellView {
   const int32_t* __restrict__ sptr = nullptr;  // [nslices + 1] entry offsets (multiples of 32)
   const int32_t* __restrict__ col = nullptr;   // [sptr[nslices]]
   const TV* __restrict__ val = nullptr;        // [sptr[nslices]]
-  int32_t long_rows = 0;  // mean slice width >= 8: the kernels take the grouped path
+  int32_t long_rows = 0;  // 0: one entry at a time; else the group size G of the grouped path (8 or 9)
 };
 
 // Apply epi(row, (A x)[row], x[row]) for every row; warps of the grid take
 // slices in a grid-stride loop.  Values TV are widened to T, the type of x
 // and of the row sums.  All 32 lanes must call this function together.
 // LONG selects the grouped path for long rows (it needs more registers, so
-// short-row matrices use a separate instance).
-template <bool OWN_X, bool LONG, class T, class TV, class Epi>
+// short-row matrices use a separate instance); G is its group size, the
+// entries per lane loaded before their FMAs.  A group that runs past the
+// slice width still issues its predicated FMAs, and on GB300 every float64
+// warp instruction costs pipe time, so the plan picks the G that wastes the
+// fewest (27-point rows: G = 9, three whole groups, against 32 slots for 27
+// entries with G = 8; measured 228 against 256 us per launch at 160^3).
+template <bool OWN_X, bool LONG, class T, int G = 8, class TV, class Epi>
 __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __restrict__ x, Epi epi) {
-  constexpr int G = 8;  // entries per lane loaded before their FMAs (long rows)
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);

@@ -802,7 +802,9 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
                        P->n);
   }
   SellLayout L;
-  if (P->mode != APCG_MODE_PERSISTENT) APCG_TRY(sell_layout(ctx->stream, P->n, A->rowptr, &L));
+  std::vector<int32_t> rp;
+  APCG_TRY(csr_check(ctx, A, &rp));
+  if (P->mode != APCG_MODE_PERSISTENT) APCG_TRY(sell_layout_host(P->n, rp, &L));
   const int sms = ctx_num_sms(ctx);
   P->long_rows = L.long_rows != 0;
   const int64_t slices = ((int64_t)P->n + 31) / 32;

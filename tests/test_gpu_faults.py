@@ -148,3 +148,44 @@ def test_bad_arguments_are_rejected_before_enqueue(ctx):
     assert res["reason"] == "converged"
     for h, f in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (vs, "apcg_vec_destroy"), (M, "apcg_mat_destroy")):
         apcg.call(f, V(h))
+
+
+def _malformed(kind):
+    A, b = _system(12)
+    rowptr, col = A.rowptr.copy(), A.col.copy()
+    if kind == "rowptr_decreasing":
+        rowptr[40] = rowptr[41] + 1
+    elif kind == "rowptr_end":
+        rowptr[-1] -= 1
+    elif kind == "col_high":
+        col[57] = A.n + 3
+    else:
+        col[3] = -1
+    return A, b, rowptr, col
+
+
+@pytest.mark.parametrize("kind", ["rowptr_decreasing", "rowptr_end", "col_high", "col_negative"])
+@pytest.mark.parametrize("solver,mode", [("cg", "host_sync"), ("cg", "async_graph"), ("cg", "persistent"),
+                                         ("tfqmr", "async_graph"), ("tfqmr", "persistent"), ("ir", None)])
+def test_malformed_csr_is_rejected_at_plan_creation(ctx, kind, solver, mode):
+    """The arrays have their declared sizes; only their contents break the CSR rules.  Plan creation reads the
+    row pointers on the host and the column indices in one bounded device pass, before any kernel reads
+    through the structure, and returns an error; the context stays usable."""
+    A, b, rowptr, col = _malformed(kind)
+    keep = [_t(rowptr), _t(col), _t(A.val), _t(b), torch.zeros(A.n, dtype=torch.float64, device="cuda:0")]
+    M = apcg.mat_wrap(keep[0], keep[1], keep[2])
+    vb, vx = apcg.vec_wrap(keep[3]), apcg.vec_wrap(keep[4])
+    try:
+        with pytest.raises(apcg.ApcgError) as ei:
+            if solver == "cg":
+                apcg.cg_solve(ctx, M, vb, vx, apcg.cg_opts(rtol=1e-8, mode=mode))
+            elif solver == "tfqmr":
+                apcg.tfqmr_solve(ctx, M, vb, vx, apcg.cg_opts(rtol=1e-8, mode=mode))
+            else:
+                apcg.ir_plan_create(ctx, M, None, apcg.ir_opts(rtol=1e-10))
+        assert "CSR" in str(ei.value)
+    finally:
+        for h, f in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (M, "apcg_mat_destroy")):
+            apcg.call(f, V(h))
+    ok, _ = _cg(ctx, *_system(12), solver="cg" if solver == "ir" else solver, mode=mode or "async_graph", rtol=1e-8)
+    assert ok["reason"] == "converged"

@@ -242,3 +242,23 @@ def test_launch_floor_reports_positive_times(dev):
     assert all(0.0 < v < 1e5 for v in f.values()), f
     assert f["graph3_back_to_back_us"] <= f["graph3_sync_us"] * 1.5
     apcg.call("apcg_ctx_destroy", C.c_void_p(ctx))
+
+
+def test_views_keep_their_tensors_alive(dev):
+    """The library holds raw device pointers; the binding keeps each wrapped tensor until its view is destroyed."""
+    import gc
+    import weakref
+
+    t = torch.zeros(1000, dtype=torch.float64, device=dev)
+    r, c = torch.zeros(11, dtype=torch.int32, device=dev), torch.zeros(0, dtype=torch.int32, device=dev)
+    v = torch.zeros(0, dtype=torch.float64, device=dev)
+    refs = [weakref.ref(x) for x in (t, r, c, v)]
+    hv = apcg.vec_wrap(t)
+    hm = apcg.mat_wrap(r, c, v)
+    del t, r, c, v
+    gc.collect()
+    assert all(w() is not None for w in refs)
+    apcg.call("apcg_vec_destroy", V(hv))
+    apcg.call("apcg_mat_destroy", V(hm))
+    gc.collect()
+    assert all(w() is None for w in refs)
