@@ -250,10 +250,10 @@ APCG_API apcg_status apcg_vec_destroy(apcg_vec v);
  * device memory: rowptr[nrows+1] (int32, rowptr[0] = 0, non-decreasing),
  * col[nnz] (int32 in [0, ncols)), val[nnz] of `dtype`.  Column indices
  * need not be sorted, but the row sums are formed in storage order.
- * Wrapping checks nothing on the device.  The CG, TFQMR and refinement plans
- * check the structure when they are created (rowptr copied back: starts at
- * 0, never decreases, ends at nnz; column indices in [0, ncols) by a device
- * pass) and return APCG_ERR_INVALID_ARG before any kernel reads through it.
+ * Wrapping checks nothing.  The CG, TFQMR and refinement plans check the
+ * structure on the device when they are created (rowptr starts at 0, never
+ * decreases and ends at nnz; column indices lie in [0, ncols)) and return
+ * APCG_ERR_INVALID_ARG before any kernel reads through it.
  * The asynchronous operations (apcg_mat_mult_async, apcg_pc_jacobi_setup_async)
  * and the batched plans, which take raw CSR arrays, trust the structure:
  * call apcg_mat_validate first where it may be malformed.

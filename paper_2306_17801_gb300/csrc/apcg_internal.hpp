@@ -51,7 +51,7 @@ Counters& counters();
 constexpr int kEventRing = 128;
 
 // Device-side error word of a context: kernels OR flags into it.
-enum : int32_t { kDevErrBadDiagonal = 1, kDevErrNonFinite = 2, kDevErrTimeout = 4, kDevErrBadIndex = 8 };
+enum : int32_t { kDevErrBadDiagonal = 1, kDevErrNonFinite = 2, kDevErrTimeout = 4 };
 
 struct ReduceScratch {
   double* partials = nullptr;  // [kMaxPartials * 3]
@@ -140,6 +140,11 @@ class OpScope {
 apcg_status ensure_scratch(apcg_ctx ctx);
 apcg_status ctx_check_device_error(apcg_ctx ctx);
 int ctx_num_sms(apcg_ctx ctx);
+// Stream-ordered device allocation from the library's memory pool (one per device, created on first use).
+// The pool keeps freed memory for reuse instead of handing it back to the driver at every synchronisation,
+// so plans created and destroyed per call (the host-buffer solve) do not map fresh pages each time.
+// Free with cudaFreeAsync.
+apcg_status dev_alloc_async(void** p, size_t bytes, cudaStream_t s);
 
 // Registry of memory IDs (creates on first registration).
 apcg_id register_memory(const void* p, size_t bytes);

@@ -255,7 +255,7 @@ apcg_status create_plan(apcg_ctx ctx_in, int32_t nsys, const int32_t* sys_row_of
   size_t b_cls = 0;
   for (auto& c : P->classes) b_cls += up(sizeof(int32_t) * c.sys.size()) + 256;
   char* ws = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&ws, b_desc + b_res + b_cls, ctx->stream));
+  APCG_TRY(dev_alloc_async((void**)&ws, b_desc + b_res + b_cls, ctx->stream));
   P->ws = ws;
   P->d_sys = reinterpret_cast<SysDesc*>(ws);
   P->d_res = reinterpret_cast<SysResult*>(ws + b_desc);
@@ -352,7 +352,7 @@ apcg_status apcg_batch_plan_tune(apcg_batch_plan P, const double* b, char* table
   APCG_CHECK(P->N == 0 || b, "b is NULL");
   cudaStream_t s = P->ctx->stream;
   double* xs = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&xs, sizeof(double) * (size_t)std::max<int64_t>(P->N, 1), s));
+  APCG_TRY(dev_alloc_async((void**)&xs, sizeof(double) * (size_t)std::max<int64_t>(P->N, 1), s));
   cudaEvent_t e0, e1;
   APCG_CUDA(cudaEventCreate(&e0));
   APCG_CUDA(cudaEventCreate(&e1));

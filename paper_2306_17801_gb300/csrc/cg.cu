@@ -306,9 +306,7 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
   // The iteration kernels read a sliced-ELL copy of A (sell.cuh); the cluster kernel reads the CSR itself.
   SellLayout L;
   const bool need_sell = A && P->mode != APCG_MODE_PERSISTENT;
-  std::vector<int32_t> rp;
-  if (A) APCG_TRY(csr_check(ctx, A, &rp));
-  if (need_sell) APCG_TRY(sell_layout_host(c.n, rp, &L));
+  if (A) APCG_TRY(csr_layout(ctx, A, need_sell, &L));
   // Workspace: dinv, r, p, w, z, partials, state, histories, cluster bookkeeping (one stream-ordered block).
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(double) * (size_t)(c.n > 0 ? c.n : 1));
@@ -321,7 +319,7 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
                                  : 0;
   const size_t total = 5 * nv + npart + nst + 2 * nh + nsysb + nsell;
   char* ws = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
+  APCG_TRY(dev_alloc_async((void**)&ws, total, ctx->stream));
   P->ws = ws;
   c.dinv = reinterpret_cast<double*>(ws);
   c.r = reinterpret_cast<double*>(ws + nv);
@@ -344,7 +342,7 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
     int32_t* scol = reinterpret_cast<int32_t*>(q);
     q += up(sizeof(int32_t) * (size_t)L.padded);
     double* sval = reinterpret_cast<double*>(q);
-    APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice,
+    APCG_CUDA(cudaMemcpyAsync(sptr, L.d_sptr, sizeof(int32_t) * ((size_t)L.nslices + 1), cudaMemcpyDeviceToDevice,
                               ctx->stream));
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
                                        scol, sval));
@@ -526,7 +524,7 @@ apcg_status apcg_cg_solve_host(int32_t n, int64_t nnz, const int32_t* rowptr, co
   const size_t brp = up(sizeof(int32_t) * ((size_t)n + 1)), bcol = up(sizeof(int32_t) * (size_t)nnz),
                bval = up(sizeof(double) * (size_t)nnz), bvec = up(sizeof(double) * (size_t)n);
   char* d = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&d, brp + bcol + bval + 2 * bvec + 256, s));
+  APCG_TRY(dev_alloc_async((void**)&d, brp + bcol + bval + 2 * bvec + 256, s));
   int32_t* d_rp = reinterpret_cast<int32_t*>(d);
   int32_t* d_col = reinterpret_cast<int32_t*>(d + brp);
   double* d_val = reinterpret_cast<double*>(d + brp + bcol);

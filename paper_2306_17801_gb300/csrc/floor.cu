@@ -74,7 +74,7 @@ apcg_status apcg_launch_floor(apcg_ctx ctx_in, int32_t reps, double* us) {
   // an 8-byte device-to-host copy and wait (what a host-synchronous iteration pays per reduction)
   double* d = nullptr;
   double* h = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&d, sizeof(double), s));
+  APCG_TRY(dev_alloc_async((void**)&d, sizeof(double), s));
   e = cudaMallocHost((void**)&h, sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(double), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

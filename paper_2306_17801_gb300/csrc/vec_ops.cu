@@ -11,7 +11,6 @@
 
 #include "apcg_internal.hpp"
 #include "cg_internal.hpp"
-#include "sell.hpp"
 #include "kernels_common.cuh"
 #include "spmv.cuh"
 
@@ -162,17 +161,6 @@ __global__ void jacobi_setup_kernel(const int32_t* __restrict__ rowptr, const in
   }
 }
 
-// Flags kDevErrBadIndex when an entry of col[0, nnz) lies outside [0, ncols).
-__global__ void col_range_kernel(const int32_t* __restrict__ col, int64_t nnz, int32_t ncols, int32_t* err) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  bool bad = false;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
-    const int32_t c = __ldg(col + e);
-    bad |= (c < 0) | (c >= ncols);
-  }
-  if (__any_sync(dev::kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kDevErrBadIndex);
-}
-
 // ------------------------------------------------------------------ host helpers
 
 apcg_status check_vec(apcg_vec v, const char* name) {
@@ -188,40 +176,6 @@ apcg_status same_len(apcg_vec a, apcg_vec b) {
 }
 
 }  // namespace
-
-apcg_status csr_check(apcg_ctx ctx, const apcg_mat_s* A, std::vector<int32_t>* rp_out) {
-  APCG_CHECK(A->nrows == A->ncols, "the matrix must be square (%d x %d)", A->nrows, A->ncols);
-  std::vector<int32_t> rp((size_t)A->nrows + 1);
-  if (A->nnz > 0) APCG_TRY(ensure_scratch(ctx));
-  {
-    // Both reads are ordered after every pending writer of the matrix on other contexts.  The column pass
-    // reads col[0, nnz) only, so it is safe whatever rowptr holds.
-    OpScope op(ctx);
-    op.read(A->id);
-    APCG_TRY(op.begin());
-    APCG_CUDA(cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost,
-                              ctx->stream));
-    counters().d2h_copies++;
-    counters().d2h_bytes += (int64_t)(sizeof(int32_t) * rp.size());
-    if (A->nnz > 0) {
-      const int g = (int)std::min<int64_t>((A->nnz + kVecThreads - 1) / kVecThreads, 8LL * ctx_num_sms(ctx));
-      col_range_kernel<<<g, kVecThreads, 0, ctx->stream>>>(A->col, A->nnz, A->ncols, ctx->scratch.dev_error);
-      APCG_CUDA(cudaGetLastError());
-      count_kernels(1);
-    }
-    APCG_TRY(op.finish());
-  }
-  APCG_CUDA(cudaStreamSynchronize(ctx->stream));  // plan set-up (counted as a copy, like the layout's read-back)
-  // read (and clear) the column flag before any host verdict, so that no flag outlives this call
-  const apcg_status cols = A->nnz > 0 ? ctx_check_device_error(ctx) : APCG_OK;
-  APCG_CHECK(rp[0] == 0, "CSR: rowptr[0] = %d, expected 0", rp[0]);
-  APCG_CHECK(rp[A->nrows] == A->nnz, "CSR: rowptr[nrows] = %d, expected nnz = %lld", rp[A->nrows],
-             (long long)A->nnz);
-  for (int32_t i = 0; i < A->nrows; ++i) APCG_CHECK(rp[i] <= rp[i + 1], "CSR: rowptr decreases at row %d", i);
-  APCG_TRY(cols);
-  if (rp_out) rp_out->swap(rp);
-  return APCG_OK;
-}
 
 apcg_status launch_fill(apcg_ctx ctx, double* y, int64_t n, double v) {
   copy_set_kernel<<<vec_grid(ctx, n >> 1, 1 << 20), kVecThreads, 0, ctx->stream>>>(n, y, nullptr, v);
