@@ -47,6 +47,18 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def aggregate_over_ranks(ms_total, steps, world, dist=None, device=None):
+    """Whole-job throughput of a timed region: the slowest rank's time (max over ranks; every rank solves
+    its own copy of the workload, weak scaling) and world * steps solves in that time."""
+    if dist is not None and world > 1:
+        import torch
+
+        tt = torch.tensor([float(ms_total)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    return ms_total, world * steps / (ms_total / 1e3)
+
+
 def _golden_iters():
     with open(os.path.join(ROOT, "tests", "golden", "oracle_pcg_history.json")) as f:
         return int(json.load(f)["c2_full_seed0"]["iters"])
@@ -256,14 +268,9 @@ def run_apcg(args, rank, world, local):
         e1.record(stream)
         barrier()
     c1 = apcg.get_counters()
-    ms_total = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total, value = aggregate_over_ranks(e0.elapsed_time(e1), args.steps, world, dist, dev)
     ms_step = ms_total / args.steps
     it = iters[-1]
-    value = world * args.steps / (ms_total / 1e3)
     gpu_launches = c1["kernel_launches"] - c0["kernel_launches"]
 
     out = {}
