@@ -450,7 +450,9 @@ def main():
     ap.add_argument("--impl", choices=["apcg", "reference"], default="apcg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ncu-case", action="store_true", help="only the set-up and 3 iterations, kernels launched one by one (for profilers)")
+    ap.add_argument("--ncu-case", nargs="?", const="c2", default=None, choices=NCU_CASES,
+                    help="a small fixed launch sequence for profilers (default c2: the set-up and 3 iterations of "
+                         "the benchmark workload, kernels launched one by one)")
     ap.add_argument("--config", choices=["c2", "c3", "c4", "c5", "tfqmr", "stencil"], default="c2",
                     help="c2: the headline 128^3 workload (default); c3/c4/c5/tfqmr/stencil: extra measurement lines")
     ap.add_argument("--no-tune", action="store_true", help="c4/c5: skip the batched autotuner")
@@ -471,7 +473,7 @@ def main():
         while not _build.up_to_date() and time.time() < deadline:
             time.sleep(1)
     if args.ncu_case:
-        ncu_case()
+        ncu_case(args.ncu_case)
         return
     if args.config != "c2":
         {"c3": bench_c3, "c4": bench_c4, "c5": bench_c5, "tfqmr": bench_tfqmr, "stencil": bench_stencil}[args.config](args)
@@ -876,29 +878,63 @@ def bench_tfqmr(args):
     print(json.dumps(line), flush=True)
 
 
-def ncu_case():
-    """Set-up kernel plus 3 iterations of the benchmark workload, each kernel launched on its own."""
+NCU_CASES = ("c2", "c3", "c1p", "tfqmr", "stencil")
+
+
+def ncu_case(case="c2"):
+    """Small, fixed launch sequences for profilers, each kernel launched on its own:
+    c2      set-up kernel + 3 CG iterations on the 128^3 7-point benchmark system (sliced-ELL K1/K2/K3);
+    c3      the same on the 160^3 27-point variable-coefficient system (long-row K1, groups of 9);
+    c1p     one whole-solve cluster launch on the 64^2 5-point system (persistent mode);
+    tfqmr   set-up + 3 TFQMR iterations on the 128^3 7-point system (async mode);
+    stencil set-up + 3 CG iterations with the matrix-free 7-point operator on 128^3."""
     import ctypes as C
 
     import numpy as np
     import torch
 
     from paper_2306_17801_gb300 import apcg
-    from synthetic import single_problem
+    from synthetic import rhs_from_solution, single_problem, stencil_matrix, stencil_terms
 
+    V = C.c_void_p
     dev = torch.device("cuda", 0)
     apcg.load()
-    p = single_problem("c2", seed=0)
+    ctx = apcg.ctx_create()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    if case == "stencil":
+        dims = (128, 128, 128)
+        Am = stencil_matrix("7pt", dims)
+        b = rhs_from_solution(Am, np.random.default_rng(0).uniform(-1, 1, Am.n))
+        bt, x = t(b), torch.zeros(Am.n, dtype=torch.float64, device=dev)
+        vb, vx = apcg.vec_wrap(bt), apcg.vec_wrap(x)
+        offs, w = stencil_terms("7pt", dims)
+        S = apcg.stencil_create(dims, offs, w)
+        plan = apcg.cg_plan_create_stencil(ctx, S, apcg.cg_opts(rtol=RTOL, check_every=K_CHECK, mode="async"))
+        apcg.call("apcg_stencil_destroy", V(S))
+        ms = apcg.cg_plan_profile(plan, vb, vx, 3)
+        apcg.call("apcg_cg_plan_destroy", V(plan))
+        print(json.dumps({"ncu_case": case, "kernel_ms": ms}))
+        return
+    p = single_problem({"c2": "c2", "c3": "c3", "c1p": "c1", "tfqmr": "c2"}[case], seed=0)
     rowptr, col, val, b = t(p.A.rowptr), t(p.A.col), t(p.A.val), t(p.b)
     x = torch.zeros(p.n, dtype=torch.float64, device=dev)
-    ctx = apcg.ctx_create()
     A = apcg.mat_wrap(rowptr, col, val)
     vb, vx = apcg.vec_wrap(b), apcg.vec_wrap(x)
-    plan = apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=RTOL, check_every=K_CHECK, mode="async", max_it=MAX_IT))
-    ms = apcg.cg_plan_profile(plan, vb, vx, 3)
-    apcg.call("apcg_cg_plan_destroy", C.c_void_p(plan))
-    print(json.dumps({"ncu_case": "c2 setup + 3 iterations", "kernel_ms": ms}))
+    if case in ("c2", "c3"):
+        plan = apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=RTOL, check_every=K_CHECK, mode="async", max_it=MAX_IT))
+        ms = apcg.cg_plan_profile(plan, vb, vx, 3)
+        apcg.call("apcg_cg_plan_destroy", V(plan))
+        print(json.dumps({"ncu_case": f"{case} setup + 3 iterations", "kernel_ms": ms}))
+    elif case == "c1p":
+        plan = apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=RTOL, check_every=1, mode="persistent"))
+        r = apcg.cg_plan_solve(plan, vb, vx)
+        apcg.call("apcg_cg_plan_destroy", V(plan))
+        print(json.dumps({"ncu_case": case, "iters": r["iters"], "kernel_launches": r["kernel_launches"]}))
+    else:
+        plan = apcg.tfqmr_plan_create(ctx, A, apcg.cg_opts(rtol=0.0, check_every=1, mode="async", max_it=3))
+        r = apcg.tfqmr_plan_solve(plan, vb, vx)
+        apcg.call("apcg_tfqmr_plan_destroy", V(plan))
+        print(json.dumps({"ncu_case": case, "iters": r["iters"], "kernel_launches": r["kernel_launches"]}))
 
 
 if __name__ == "__main__":

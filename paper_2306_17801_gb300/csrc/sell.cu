@@ -77,13 +77,29 @@ __global__ void slice_width_kernel(int32_t n, int64_t nnz, int32_t nslices, cons
       mw = max(mw, w);
     }
   }
+  // one set of atomics per block (the counters are integers, so the order of the adds does not matter)
+  __shared__ unsigned long long s_pad, s_s8, s_s9;
+  __shared__ int32_t s_mw, s_bad;
+  if (threadIdx.x == 0) {
+    s_pad = s_s8 = s_s9 = 0ull;
+    s_mw = s_bad = 0;
+  }
+  __syncthreads();
   const bool any_bad = __any_sync(dev::kFull, bad);
   if (lane == 0) {
-    if (pad) atomicAdd(&st->padded, pad);
-    if (s8) atomicAdd(&st->slots8, s8);
-    if (s9) atomicAdd(&st->slots9, s9);
-    if (mw) atomicMax(&st->max_width, mw);
-    if (any_bad) atomicOr(&st->bad, kBadRowptr);
+    if (pad) atomicAdd(&s_pad, pad);
+    if (s8) atomicAdd(&s_s8, s8);
+    if (s9) atomicAdd(&s_s9, s9);
+    if (mw) atomicMax(&s_mw, mw);
+    if (any_bad) atomicOr(&s_bad, kBadRowptr);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_pad) atomicAdd(&st->padded, s_pad);
+    if (s_s8) atomicAdd(&st->slots8, s_s8);
+    if (s_s9) atomicAdd(&st->slots9, s_s9);
+    if (s_mw) atomicMax(&st->max_width, s_mw);
+    if (s_bad) atomicOr(&st->bad, s_bad);
   }
 }
 

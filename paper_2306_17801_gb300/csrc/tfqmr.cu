@@ -250,9 +250,12 @@ __global__ void __launch_bounds__(kThreads, 4) t1_kernel(TqArgs a, HostScalars h
 }
 
 // T2, the even half-step: q = M u2 and the updates, ||w||^2 and (w, r*); the
-// test and beta in the last block.
+// test and beta in the last block.  Bounded to 40 registers (six blocks per
+// SM, a few bytes of spill): the extra resident warps hide more of the SpMV's
+// gather latency (128^3 7-point: 173 against 180 us per iteration at 48
+// registers and five blocks).  T3 runs on its own grid at its own occupancy.
 template <bool HOST, bool LONG>
-__global__ void __launch_bounds__(kThreads) t2_kernel(TqArgs a, HostScalars h, cudaGraphConditionalHandle cond,
+__global__ void __launch_bounds__(kThreads, 6) t2_kernel(TqArgs a, HostScalars h, cudaGraphConditionalHandle cond,
                                                       int32_t use_cond) {
   if (!HOST && read_done(a.st)) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -397,7 +400,7 @@ struct apcg_tfqmr_plan_s {
   int32_t mode = APCG_MODE_ASYNC_GRAPH;
   apcg::tq::TqArgs a{};  // x is filled in per solve
   int32_t n = 0, k = 1, max_it = 0, hist_len = 0;
-  int grid_spmv = 1, grid_vec = 1;
+  int grid_spmv = 1, grid_vec = 1, grid_t3 = 1;  // t3 takes fewer registers than t2: its own persistent grid
   bool long_rows = false;
   char* ws = nullptr;
   apcg::tq::TqState* st_host = nullptr;  // pinned mirror of the state block
@@ -476,11 +479,11 @@ apcg_status launch_t2(Plan P, double* x, cudaStream_t s, bool host, const HostSc
 apcg_status launch_t3(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h) {
   const TqArgs a = args_for(P, x);
   if (host)
-    P->long_rows ? t3_kernel<true, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h)
-                 : t3_kernel<true, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h);
+    P->long_rows ? t3_kernel<true, true><<<P->grid_t3, kThreads, 0, s>>>(a, h)
+                 : t3_kernel<true, false><<<P->grid_t3, kThreads, 0, s>>>(a, h);
   else
-    P->long_rows ? t3_kernel<false, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h)
-                 : t3_kernel<false, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h);
+    P->long_rows ? t3_kernel<false, true><<<P->grid_t3, kThreads, 0, s>>>(a, h)
+                 : t3_kernel<false, false><<<P->grid_t3, kThreads, 0, s>>>(a, h);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -808,6 +811,8 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   const int64_t slices = ((int64_t)P->n + 31) / 32;
   P->grid_spmv = P->long_rows ? occupancy_grid(t2_kernel<false, true>, sms, (slices + 7) / 8)
                               : occupancy_grid(t2_kernel<false, false>, sms, (slices + 7) / 8);
+  P->grid_t3 = P->long_rows ? occupancy_grid(t3_kernel<false, true>, sms, (slices + 7) / 8)
+                            : occupancy_grid(t3_kernel<false, false>, sms, (slices + 7) / 8);
   P->grid_vec = occupancy_grid(t1_kernel<false>, sms, ((int64_t)P->n / 2 + kThreads - 1) / kThreads);
   // Workspace: dinv, r*, u, u2, w, d, v, p, q; partials; state; histories; sliced-ELL copy.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
