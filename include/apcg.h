@@ -356,20 +356,25 @@ typedef struct {
  * scaling, Sec. 4.1-4.2; loop body in the order of the mixed-API CG example
  * of Sec. 3.3, with the standard initialisation r = b - A x0, z = D^-1 r,
  * p = z).  A is square float64 with a nonzero diagonal; x holds x0 on entry
- * and the iterate on exit.  Marks A and b read, x read-write.  Blocks the
- * host once, at the end, to fill *res.  Returns APCG_ERR_BAD_DIAGONAL for a
- * zero, missing or non-finite diagonal entry, and APCG_OK otherwise (a
- * breakdown or the iteration cap is reported in res->reason).
+ * and the iterate on exit.  Marks A and b read, x read-write.  One call is
+ * apcg_cg_plan_create + apcg_cg_plan_solve + destroy: the set-up blocks the
+ * host while it checks and converts the matrix, the solve once, at the end,
+ * to fill *res.  Returns APCG_ERR_INVALID_ARG for a malformed CSR structure,
+ * APCG_ERR_BAD_DIAGONAL for a zero, missing or non-finite diagonal entry, and
+ * APCG_OK otherwise (a breakdown or the iteration cap is reported in
+ * res->reason).
  */
 APCG_API apcg_status apcg_cg_solve(apcg_ctx ctx, apcg_mat A, apcg_vec b, apcg_vec x, const apcg_cg_opts* opts,
                           apcg_cg_result* res);
 
 /*
- * Reusable solver plan: set-up once per matrix and option set (Jacobi
- * diagonal, workspace, launch shapes, captured graphs), then any number of
- * solves.  The plan keeps non-owning references to A.  A plan's solves on
- * one context are ordered; the plan must not be used from two contexts at
- * once.
+ * Reusable solver plan: set-up once per matrix and option set (structure
+ * check, sliced-ELL copy, Jacobi diagonal, workspace, launch shapes, captured
+ * graphs), then any number of solves.  Creation runs on the context's stream
+ * and blocks the host until it is done; it returns APCG_ERR_INVALID_ARG for a
+ * malformed CSR structure and APCG_ERR_BAD_DIAGONAL for a bad diagonal.  The
+ * plan keeps non-owning references to A.  A plan's solves on one context are
+ * ordered; the plan must not be used from two contexts at once.
  */
 APCG_API apcg_status apcg_cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, apcg_cg_plan* out);
 APCG_API apcg_status apcg_cg_plan_solve(apcg_cg_plan plan, apcg_vec b, apcg_vec x, apcg_cg_result* res);
