@@ -351,7 +351,7 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
     c.A.sptr = sptr;
     c.A.col = scol;
     c.A.val = sval;
-    c.A.long_rows = L.long_rows;
+    c.A.long_rows = L.group;  // the float64 SpMV's group size (K1 and the set-up kernel)
     core_configure(c, A->nnz, ctx_num_sms(ctx));  // the SpMV kernel instance depends on the row length
   }
   SysDesc d0{};

@@ -381,16 +381,21 @@ apcg_status k1_stencil_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream
   return APCG_OK;
 }
 
-// Groups of 9 in the float64 K1 only: the float32 inner solves are bound by HBM, not by wasted FMA slots,
-// and the larger groups cost them occupancy (refinement at 160^3: 110.2 against 107.3 ms).
-template <class T>
-constexpr bool kGroup9 = std::is_same<T, double>::value;
-
-// The K1 instance for the plan's layout (short rows, groups of 8, groups of 9).
+// The K1 instance for the plan's layout: one entry at a time, or groups of G.  The float64 plans choose G in
+// 5..9 (csr_layout); the float32 inner solves of the refinement keep 0 or 8: they are bound by HBM, not by
+// wasted FMA slots, and larger groups cost them occupancy (refinement at 160^3 with groups of 9: 110.2
+// against 107.3 ms).
 template <bool HOST, class T>
 void* k1_instance(const CgCore<T>& c) {
-  if constexpr (kGroup9<T>)
-    if (c.A.long_rows == 9) return (void*)k1_kernel<HOST, true, T, 9>;
+  if constexpr (std::is_same<T, double>::value) {
+    switch (c.A.long_rows) {
+      case 5: return (void*)k1_kernel<HOST, true, T, 5>;
+      case 6: return (void*)k1_kernel<HOST, true, T, 6>;
+      case 7: return (void*)k1_kernel<HOST, true, T, 7>;
+      case 9: return (void*)k1_kernel<HOST, true, T, 9>;
+      default: break;
+    }
+  }
   return c.A.long_rows ? (void*)k1_kernel<HOST, true, T> : (void*)k1_kernel<HOST, false, T>;
 }
 

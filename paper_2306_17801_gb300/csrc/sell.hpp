@@ -18,6 +18,7 @@ struct SellLayout {
   int32_t nslices = 0;
   int64_t padded = 0;          // entries including padding (multiple of 32)
   int32_t long_rows = 0;       // 0: mean slice width < 8; else the group size of the grouped SpMV (8 or 9)
+  int32_t group = 0;           // float64 CG SpMV: 0 (one entry at a time) or its group size, 5..9
   int32_t max_width = 0;       // entries per row of the widest slice
   int32_t* d_sptr = nullptr;   // [nslices + 1] slice offsets on the device (inside d_block), or null
   void* d_block = nullptr;
