@@ -250,13 +250,14 @@ __global__ void __launch_bounds__(kThreads, 4) t1_kernel(TqArgs a, HostScalars h
 }
 
 // T2, the even half-step: q = M u2 and the updates, ||w||^2 and (w, r*); the
-// test and beta in the last block.  Bounded to 40 registers (six blocks per
-// SM, a few bytes of spill): the extra resident warps hide more of the SpMV's
-// gather latency (128^3 7-point: 173 against 180 us per iteration at 48
+// test and beta in the last block.  G: the SpMV's group size (0: one entry at
+// a time).  The one-at-a-time instance is bounded to 40 registers (six blocks
+// per SM, a few bytes of spill): the extra resident warps hide more of the
+// gathers' latency (128^3 7-point: 173 against 180 us per iteration at 48
 // registers and five blocks).  T3 runs on its own grid at its own occupancy.
-template <bool HOST, bool LONG>
-__global__ void __launch_bounds__(kThreads, 6) t2_kernel(TqArgs a, HostScalars h, cudaGraphConditionalHandle cond,
-                                                      int32_t use_cond) {
+template <bool HOST, int G>
+__global__ void __launch_bounds__(kThreads, G == 0 ? 6 : 4) t2_kernel(TqArgs a, HostScalars h,
+                                                                   cudaGraphConditionalHandle cond, int32_t use_cond) {
   if (!HOST && read_done(a.st)) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
       a.st->body_runs += 1;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 6) t2_kernel(TqArgs a, HostScalars h
   const double ex = HOST ? h.eta_x : a.st->eta_x;
   __shared__ double red[2 * kThreads];
   double v[2] = {0.0, 0.0};
-  dev::sell_spmv<true, LONG, double>(a.A, a.u2, [&](int32_t i, double au2, double u2i) {
+  dev::sell_spmv<true, (G > 0), double, (G > 0 ? G : 8)>(a.A, a.u2, [&](int32_t i, double au2, double u2i) {
                                           const double qi = __ldg(a.dinv + i) * au2;
                                           double di = a.d[i];
                                           if (pend) a.x[i] = fma(ex, di, a.x[i]);
@@ -320,13 +321,13 @@ __global__ void __launch_bounds__(kThreads, 6) t2_kernel(TqArgs a, HostScalars h
 
 // T3, the direction update: u = w + beta u2;  p = M w + beta q (= M u);
 // v = p + beta (q + beta v);  sigma = (v, r*) and alpha in the last block.
-template <bool HOST, bool LONG>
+template <bool HOST, int G>
 __global__ void __launch_bounds__(kThreads) t3_kernel(TqArgs a, HostScalars h) {
   if (!HOST && read_done(a.st)) return;
   const double beta = HOST ? h.beta : a.st->beta;
   __shared__ double red[kThreads];
   double v[1] = {0.0};
-  dev::sell_spmv<true, LONG, double>(a.A, a.w, [&](int32_t i, double aw, double wi) {
+  dev::sell_spmv<true, (G > 0), double, (G > 0 ? G : 8)>(a.A, a.w, [&](int32_t i, double aw, double wi) {
                                           const double mwi = __ldg(a.dinv + i) * aw;
                                           const double qi = a.q[i];
                                           a.u[i] = fma(beta, a.u2[i], wi);
@@ -401,7 +402,8 @@ struct apcg_tfqmr_plan_s {
   apcg::tq::TqArgs a{};  // x is filled in per solve
   int32_t n = 0, k = 1, max_it = 0, hist_len = 0;
   int grid_spmv = 1, grid_vec = 1, grid_t3 = 1;  // t3 takes fewer registers than t2: its own persistent grid
-  bool long_rows = false;
+  bool long_rows = false;  // the set-up kernels' SpMV path
+  int group = 0;           // the iteration kernels' SpMV group size (0: one entry at a time)
   char* ws = nullptr;
   apcg::tq::TqState* st_host = nullptr;  // pinned mirror of the state block
   apcg_id id = 0;
@@ -463,28 +465,46 @@ apcg_status launch_t1(Plan P, double* x, cudaStream_t s, bool host, const HostSc
   return APCG_OK;
 }
 
+// The instance of T2 or T3 for the plan's group size.
+template <bool HOST>
+void* t2_instance(int g) {
+  switch (g) {
+    case 5: return (void*)t2_kernel<HOST, 5>;
+    case 6: return (void*)t2_kernel<HOST, 6>;
+    case 7: return (void*)t2_kernel<HOST, 7>;
+    case 8: return (void*)t2_kernel<HOST, 8>;
+    case 9: return (void*)t2_kernel<HOST, 9>;
+    default: return (void*)t2_kernel<HOST, 0>;
+  }
+}
+template <bool HOST>
+void* t3_instance(int g) {
+  switch (g) {
+    case 5: return (void*)t3_kernel<HOST, 5>;
+    case 6: return (void*)t3_kernel<HOST, 6>;
+    case 7: return (void*)t3_kernel<HOST, 7>;
+    case 8: return (void*)t3_kernel<HOST, 8>;
+    case 9: return (void*)t3_kernel<HOST, 9>;
+    default: return (void*)t3_kernel<HOST, 0>;
+  }
+}
+
 apcg_status launch_t2(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h,
                       cudaGraphConditionalHandle cond, int32_t use_cond) {
-  const TqArgs a = args_for(P, x);
-  if (host)
-    P->long_rows ? t2_kernel<true, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond)
-                 : t2_kernel<true, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond);
-  else
-    P->long_rows ? t2_kernel<false, true><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond)
-                 : t2_kernel<false, false><<<P->grid_spmv, kThreads, 0, s>>>(a, h, cond, use_cond);
-  APCG_CUDA(cudaGetLastError());
+  TqArgs a = args_for(P, x);
+  HostScalars hh = h;
+  void* args[] = {&a, &hh, &cond, &use_cond};
+  void* k = host ? t2_instance<true>(P->group) : t2_instance<false>(P->group);
+  APCG_CUDA(cudaLaunchKernel(k, dim3(P->grid_spmv), dim3(kThreads), args, 0, s));
   return APCG_OK;
 }
 
 apcg_status launch_t3(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h) {
-  const TqArgs a = args_for(P, x);
-  if (host)
-    P->long_rows ? t3_kernel<true, true><<<P->grid_t3, kThreads, 0, s>>>(a, h)
-                 : t3_kernel<true, false><<<P->grid_t3, kThreads, 0, s>>>(a, h);
-  else
-    P->long_rows ? t3_kernel<false, true><<<P->grid_t3, kThreads, 0, s>>>(a, h)
-                 : t3_kernel<false, false><<<P->grid_t3, kThreads, 0, s>>>(a, h);
-  APCG_CUDA(cudaGetLastError());
+  TqArgs a = args_for(P, x);
+  HostScalars hh = h;
+  void* args[] = {&a, &hh};
+  void* k = host ? t3_instance<true>(P->group) : t3_instance<false>(P->group);
+  APCG_CUDA(cudaLaunchKernel(k, dim3(P->grid_t3), dim3(kThreads), args, 0, s));
   return APCG_OK;
 }
 
@@ -808,11 +828,10 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   APCG_TRY(csr_layout(ctx, A, P->mode != APCG_MODE_PERSISTENT, &L));
   const int sms = ctx_num_sms(ctx);
   P->long_rows = L.long_rows != 0;
+  P->group = L.group;
   const int64_t slices = ((int64_t)P->n + 31) / 32;
-  P->grid_spmv = P->long_rows ? occupancy_grid(t2_kernel<false, true>, sms, (slices + 7) / 8)
-                              : occupancy_grid(t2_kernel<false, false>, sms, (slices + 7) / 8);
-  P->grid_t3 = P->long_rows ? occupancy_grid(t3_kernel<false, true>, sms, (slices + 7) / 8)
-                            : occupancy_grid(t3_kernel<false, false>, sms, (slices + 7) / 8);
+  P->grid_spmv = occupancy_grid(t2_instance<false>(P->group), sms, (slices + 7) / 8);
+  P->grid_t3 = occupancy_grid(t3_instance<false>(P->group), sms, (slices + 7) / 8);
   P->grid_vec = occupancy_grid(t1_kernel<false>, sms, ((int64_t)P->n / 2 + kThreads - 1) / kThreads);
   // Workspace: dinv, r*, u, u2, w, d, v, p, q; partials; state; histories; sliced-ELL copy.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
