@@ -314,7 +314,9 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
   const size_t nst = up(sizeof(CgState));
   const size_t nh = up(sizeof(double) * (size_t)(c.hist_len > 0 ? c.hist_len : 1));
   const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
-  const size_t nsell = need_sell ? up(sizeof(int32_t) * ((size_t)L.nslices + 1)) + up(sizeof(int32_t) * (size_t)L.padded) +
+  // column indices as 16-bit offsets from the row where they fit (2 bytes per entry less in every SpMV)
+  const size_t colw = L.d16 ? sizeof(int16_t) : sizeof(int32_t);
+  const size_t nsell = need_sell ? up(sizeof(int32_t) * ((size_t)L.nslices + 1)) + up(colw * (size_t)L.padded) +
                                        up(sizeof(double) * (size_t)L.padded)
                                  : 0;
   const size_t total = 5 * nv + npart + nst + 2 * nh + nsysb + nsell;
@@ -339,17 +341,19 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
     char* q = tail + nsysb;
     int32_t* sptr = reinterpret_cast<int32_t*>(q);
     q += up(sizeof(int32_t) * ((size_t)L.nslices + 1));
-    int32_t* scol = reinterpret_cast<int32_t*>(q);
-    q += up(sizeof(int32_t) * (size_t)L.padded);
+    int32_t* scol = L.d16 ? nullptr : reinterpret_cast<int32_t*>(q);
+    int16_t* sdcol = L.d16 ? reinterpret_cast<int16_t*>(q) : nullptr;
+    q += up(colw * (size_t)L.padded);
     double* sval = reinterpret_cast<double*>(q);
     APCG_CUDA(cudaMemcpyAsync(sptr, L.d_sptr, sizeof(int32_t) * ((size_t)L.nslices + 1), cudaMemcpyDeviceToDevice,
                               ctx->stream));
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
-                                       scol, sval));
+                                       scol, sdcol, sval));
     c.A.n = c.n;
     c.A.nslices = L.nslices;
     c.A.sptr = sptr;
     c.A.col = scol;
+    c.A.dcol = sdcol;
     c.A.val = sval;
     c.A.long_rows = L.group;  // the float64 SpMV's group size (K1 and the set-up kernel)
     core_configure(c, A->nnz, ctx_num_sms(ctx));  // the SpMV kernel instance depends on the row length

@@ -175,6 +175,9 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   P->grid_upd = std::max(1, std::min(sms * 8, (int)((P->n / 4 + kThreads - 1) / kThreads)));
   SellLayout L;
   APCG_TRY(csr_layout(ctx, &S, true, &L));
+  // 32-bit column indices here even where 16-bit offsets would fit: the float32 inner SpMV is bound by HBM at
+  // six blocks per SM, and the offset form's extra registers cost it one (160^3 27-point refinement: 108.8
+  // against 107.8 ms).
   // Workspace: sliced-ELL (sptr, col, float32 values, float64 values if A64), dinv32, r, p, w, z, d,
   // partials and states.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -224,13 +227,13 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
                             ctx->stream));
   if (A32)
     APCG_TRY(sell_fill<float, float>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const float*>(A32->val),
-                                     scol, sval32));
+                                     scol, nullptr, sval32));
   else
     APCG_TRY(sell_fill<double, float>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const double*>(A64->val),
-                                      scol, sval32));
+                                      scol, nullptr, sval32));
   if (A64)
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const double*>(A64->val),
-                                       nullptr, sval64));
+                                       nullptr, nullptr, sval64));
   P->A32.n = P->A64.n = P->n;
   P->A32.nslices = L.nslices;
   P->A32.sptr = sptr;

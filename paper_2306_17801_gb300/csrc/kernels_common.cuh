@@ -18,6 +18,7 @@ constexpr int kMaxPartials = 4096;  // upper bound on the grid of any reducing k
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ int16_t ld_stream(const int16_t* p) { return __ldcs(p); }
 __device__ __forceinline__ double2 ld_stream2(const double2* p) { return __ldcs(p); }
 __device__ __forceinline__ float4 ld_stream2(const float4* p) { return __ldcs(p); }
 // Read-only path for gathered vector entries (L1-allocating).

@@ -10,11 +10,14 @@ namespace apcg {
 namespace {
 
 // One thread per (slice, lane): writes the row's entries k = 0..width-1 of its
-// slice, padding with value 0 and a harmless column (the row itself, or 0).
+// slice, padding with value 0 and a harmless column (the row itself, or row
+// n - 1 for the lanes past the last row), as an index (scol) or as the
+// 16-bit offset from the row (sdcol; the plan has checked that it fits).
 template <class TI, class TO>
 __global__ void sell_fill_kernel(int32_t n, int32_t nslices, const int32_t* __restrict__ sptr,
                                  const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                 const TI* __restrict__ val, int32_t* __restrict__ scol, TO* __restrict__ sval) {
+                                 const TI* __restrict__ val, int32_t* __restrict__ scol, int16_t* __restrict__ sdcol,
+                                 TO* __restrict__ sval) {
   const int64_t total = (int64_t)nslices * 32;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += stride) {
@@ -27,11 +30,13 @@ __global__ void sell_fill_kernel(int32_t n, int32_t nslices, const int32_t* __re
       e0 = rowptr[r];
       len = rowptr[r + 1] - e0;
     }
-    const int32_t pad_col = r < n ? (int32_t)r : 0;
+    const int32_t pad_col = r < n ? (int32_t)r : (n > 0 ? n - 1 : 0);
     for (int32_t k = 0; k < width; ++k) {
       const int64_t dst = (int64_t)base + 32 * (int64_t)k + lane;
       const bool real = k < len;
-      if (scol) scol[dst] = real ? col[e0 + k] : pad_col;
+      const int32_t c = real ? col[e0 + k] : pad_col;
+      if (scol) scol[dst] = c;
+      if (sdcol) sdcol[dst] = (int16_t)(c - (int32_t)r);
       if (sval) sval[dst] = real ? (TO)val[e0 + k] : TO(0);
     }
   }
@@ -43,6 +48,8 @@ enum : int32_t { kBadRowptr = 1, kBadColumn = 2 };
 constexpr int kGroupMin = 5, kGroupMax = 9, kGroups = kGroupMax - kGroupMin + 1;
 
 struct LayoutStats {
+  int32_t max_offset;                  // largest |col - row| over the entries (checked structures only)
+  int32_t pad0;
   unsigned long long padded;           // sum over slices of 32 * width
   unsigned long long slots[kGroups];   // FMA slots per lane with groups of G = kGroupMin.. (whole groups per slice)
   int32_t max_width;
@@ -106,6 +113,33 @@ __global__ void slice_width_kernel(int32_t n, int64_t nnz, int32_t nslices, cons
     if (s_mw) atomicMax(&st->max_width, s_mw);
     if (s_bad) atomicOr(&st->bad, s_bad);
   }
+}
+
+// The largest |col - row| over the entries (one warp per slice of 32 rows;
+// runs only on a structure that passed the checks above).
+__global__ void offset_range_kernel(int32_t n, int32_t nslices, const int32_t* __restrict__ rowptr,
+                                    const int32_t* __restrict__ col, LayoutStats* __restrict__ st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t m = 0;
+  for (int64_t s = w0; s < nslices; s += nw) {
+    const int64_t r = s * 32 + lane;
+    if (r < n) {
+      const int32_t e1 = rowptr[r + 1];
+      for (int32_t e = rowptr[r]; e < e1; ++e) {
+        const int32_t d = __ldg(col + e) - (int32_t)r;
+        m = max(m, d < 0 ? -d : d);
+      }
+    }
+  }
+  m = (int32_t)__reduce_max_sync(dev::kFull, (unsigned)m);
+  __shared__ int32_t s_m;
+  if (threadIdx.x == 0) s_m = 0;
+  __syncthreads();
+  if (lane == 0 && m) atomicMax(&s_m, m);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_m) atomicMax(&st->max_offset, s_m);
 }
 
 // Flags kBadColumn when an entry of col[0, nnz) lies outside [0, ncols).
@@ -273,26 +307,41 @@ apcg_status csr_layout(apcg_ctx ctx, const apcg_mat_s* A, bool want_sptr, SellLa
       if (h.slots[G - kGroupMin] < h.slots[best - kGroupMin]) best = G;
     out->group = best;
   }
+  // 16-bit column offsets where every entry lies within 32767 of its row (the structure is valid by now,
+  // so the pass may follow rowptr)
+  out->d16 = false;
+  if (A->nnz > 0) {
+    const int gw = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)out->nslices + 7) / 8, 8LL * sms));
+    offset_range_kernel<<<gw, 256, 0, ctx->stream>>>(n, out->nslices, A->rowptr, A->col, st);
+    APCG_CUDA(cudaGetLastError());
+    count_kernels(1);
+    int32_t m = 0;
+    APCG_CUDA(cudaMemcpyAsync(&m, &st->max_offset, sizeof(m), cudaMemcpyDeviceToHost, ctx->stream));
+    APCG_CUDA(cudaStreamSynchronize(ctx->stream));
+    counters().d2h_copies++;
+    counters().d2h_bytes += (int64_t)sizeof(m);
+    out->d16 = m <= 32767;
+  }
   return APCG_OK;
 }
 
 template <class TI, class TO>
 apcg_status sell_fill(cudaStream_t s, const SellLayout& L, const int32_t* d_sptr, const int32_t* rowptr,
-                      const int32_t* col, const TI* val, int32_t* scol, TO* sval) {
+                      const int32_t* col, const TI* val, int32_t* scol, int16_t* sdcol, TO* sval) {
   if (L.nslices == 0) return APCG_OK;
   const int64_t total = (int64_t)L.nslices * 32;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 65536);
-  sell_fill_kernel<TI, TO><<<grid, 256, 0, s>>>(L.n, L.nslices, d_sptr, rowptr, col, val, scol, sval);
+  sell_fill_kernel<TI, TO><<<grid, 256, 0, s>>>(L.n, L.nslices, d_sptr, rowptr, col, val, scol, sdcol, sval);
   APCG_CUDA(cudaGetLastError());
   count_kernels(1);
   return APCG_OK;
 }
 
 template apcg_status sell_fill<double, double>(cudaStream_t, const SellLayout&, const int32_t*, const int32_t*,
-                                               const int32_t*, const double*, int32_t*, double*);
+                                               const int32_t*, const double*, int32_t*, int16_t*, double*);
 template apcg_status sell_fill<double, float>(cudaStream_t, const SellLayout&, const int32_t*, const int32_t*,
-                                              const int32_t*, const double*, int32_t*, float*);
+                                              const int32_t*, const double*, int32_t*, int16_t*, float*);
 template apcg_status sell_fill<float, float>(cudaStream_t, const SellLayout&, const int32_t*, const int32_t*,
-                                             const int32_t*, const float*, int32_t*, float*);
+                                             const int32_t*, const float*, int32_t*, int16_t*, float*);
 
 }  // namespace apcg

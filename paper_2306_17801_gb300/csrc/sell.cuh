@@ -27,7 +27,8 @@ struct SellView {
   int32_t n = 0;        // rows
   int32_t nslices = 0;  // ceil(n / 32)
   const int32_t* __restrict__ sptr = nullptr;  // [nslices + 1] entry offsets (multiples of 32)
-  const int32_t* __restrict__ col = nullptr;   // [sptr[nslices]]
+  const int32_t* __restrict__ col = nullptr;   // [sptr[nslices]] column indices, or
+  const int16_t* __restrict__ dcol = nullptr;  // [sptr[nslices]] column - row (the D16 instances)
   const TV* __restrict__ val = nullptr;        // [sptr[nslices]]
   int32_t long_rows = 0;  // 0: one entry at a time; else the group size G of the grouped path (8 or 9)
 };
@@ -42,7 +43,11 @@ struct SellView {
 // warp instruction costs pipe time, so the plan picks the G that wastes the
 // fewest (27-point rows: G = 9, three whole groups, against 32 slots for 27
 // entries with G = 8; measured 228 against 256 us per launch at 160^3).
-template <bool OWN_X, bool LONG, class T, int G = 8, class TV, class Epi>
+// D16: the column of an entry is read as a 16-bit offset from its row
+// (A.dcol) instead of a 32-bit index (A.col): 2 bytes per entry less, for
+// matrices whose entries all lie within 32767 of the diagonal (the plan
+// checks).  The sums are the same.
+template <bool OWN_X, bool LONG, class T, int G = 8, bool D16 = false, class TV, class Epi>
 __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __restrict__ x, Epi epi) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -61,7 +66,8 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
     const int32_t row = (int32_t)(s * 32 + lane);
     T x_own = T(0);
     if (OWN_X && row < A.n) x_own = ld_ro(x + row);
-    const int32_t* cp = A.col + base + lane;
+    const int32_t* cp = D16 ? nullptr : A.col + base + lane;
+    const int16_t* dp = D16 ? A.dcol + base + lane : nullptr;
     const TV* vp = A.val + base + lane;
     const int32_t width = (end - base) >> 5;
     T acc = T(0);
@@ -78,7 +84,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
 #pragma unroll
         for (int g = 0; g < G; ++g) {
           const bool ok = k + g < width;
-          j[g] = ok ? ld_stream(cp + 32 * (k + g)) : 0;
+          j[g] = ok ? (D16 ? row + (int32_t)ld_stream(dp + 32 * (k + g)) : ld_stream(cp + 32 * (k + g))) : 0;
           a[g] = ok ? ld_stream(vp + 32 * (k + g)) : TV(0);
         }
 #pragma unroll
@@ -91,7 +97,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
       // Short rows (5- and 7-point stencils): one entry at a time (measured
       // faster: fewer registers, more resident warps).
       for (int32_t k = 0; k < width; ++k) {
-        const int32_t j = ld_stream(cp + 32 * k);
+        const int32_t j = D16 ? row + (int32_t)ld_stream(dp + 32 * k) : ld_stream(cp + 32 * k);
         const TV a = ld_stream(vp + 32 * k);
         acc = fma((T)a, ld_ro(x + j), acc);
       }

@@ -19,6 +19,7 @@ struct SellLayout {
   int64_t padded = 0;          // entries including padding (multiple of 32)
   int32_t long_rows = 0;       // 0: mean slice width < 8; else the group size of the grouped SpMV (8 or 9)
   int32_t group = 0;           // float64 CG SpMV: 0 (one entry at a time) or its group size, 5..9
+  bool d16 = false;            // every entry lies within 32767 of its row: 16-bit column offsets fit
   int32_t max_width = 0;       // entries per row of the widest slice
   int32_t* d_sptr = nullptr;   // [nslices + 1] slice offsets on the device (inside d_block), or null
   void* d_block = nullptr;
@@ -41,11 +42,12 @@ struct SellLayout {
 // rowptr[0, n] and col[0, nnz) only).
 apcg_status csr_layout(apcg_ctx ctx, const apcg_mat_s* A, bool want_sptr, SellLayout* out);
 
-// Scatter CSR rows into the slices: column indices (if scol != nullptr) and
-// values converted from TI to TO (if sval != nullptr).  d_sptr is the layout's
-// sptr on the device.
+// Scatter CSR rows into the slices: column indices (if scol != nullptr), column
+// offsets from the row (if sdcol != nullptr; only where L.d16) and values
+// converted from TI to TO (if sval != nullptr).  d_sptr is the layout's sptr
+// on the device.
 template <class TI, class TO>
 apcg_status sell_fill(cudaStream_t s, const SellLayout& L, const int32_t* d_sptr, const int32_t* rowptr,
-                      const int32_t* col, const TI* val, int32_t* scol, TO* sval);
+                      const int32_t* col, const TI* val, int32_t* scol, int16_t* sdcol, TO* sval);
 
 }  // namespace apcg

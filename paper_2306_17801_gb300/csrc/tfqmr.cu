@@ -874,7 +874,7 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
     APCG_CUDA(cudaMemcpyAsync(sptr, L.d_sptr, sizeof(int32_t) * ((size_t)L.nslices + 1), cudaMemcpyDeviceToDevice,
                               ctx->stream));
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
-                                       scol, sval));
+                                       scol, nullptr, sval));
   }
   char* tail = q + nsptr + ncol + nval;
   P->sys = reinterpret_cast<SysDesc*>(tail);
