@@ -400,6 +400,42 @@ APCG_API apcg_status apcg_cg_plan_destroy(apcg_cg_plan plan);
 APCG_API apcg_status apcg_cg_plan_profile(apcg_cg_plan plan, apcg_vec b, apcg_vec x, int32_t iters, float* ms);
 
 /*
+ * The sliced-ELL copy of the matrix that a plan's SpMV reads (slices of 32
+ * consecutive rows stored column-major, each padded to its widest row; the
+ * SpMV of Sec. 4.1's MatMult in a layout for 32-lane warps), for tests and
+ * performance reports.  col_format says how each stored entry's column is
+ * found:
+ *   APCG_COLS_NONE      the plan holds no copy (whole-solve cluster mode, or a
+ *                       stencil operator);
+ *   APCG_COLS_INDEX     a 32-bit column index per stored entry;
+ *   APCG_COLS_OFFSET16  a 16-bit offset from the row per stored entry (chosen
+ *                       where every entry lies within 32767 of the diagonal);
+ *   APCG_COLS_PATTERN   one list of column offsets per slice, shared by its 32
+ *                       rows; a row that lacks one of them stores the value 0
+ *                       there (chosen where every row's columns strictly
+ *                       increase and these lists pad the slices by at most
+ *                       1/16 more than their widest rows do: stencil
+ *                       matrices).  The matrix values are then the only
+ *                       per-entry stream.
+ * Every format adds each row's entries in their CSR order.  group is the
+ * SpMV's group size (entries per lane loaded before their FMAs; 0 = one at a
+ * time), nslices the number of slices, padded the stored entries including
+ * padding.  Plain host reads: never blocks.  Returns APCG_ERR_INVALID_ARG for
+ * a NULL plan or out.
+ */
+#define APCG_COLS_NONE (-1)
+#define APCG_COLS_INDEX 0
+#define APCG_COLS_OFFSET16 1
+#define APCG_COLS_PATTERN 2
+typedef struct apcg_plan_layout {
+  int32_t col_format; /* APCG_COLS_* */
+  int32_t group;      /* SpMV group size, 0 = one entry at a time */
+  int64_t nslices;    /* slices of 32 rows */
+  int64_t padded;     /* stored entries including padding */
+} apcg_plan_layout;
+APCG_API apcg_status apcg_cg_plan_layout(apcg_cg_plan plan, apcg_plan_layout* out);
+
+/*
  * The same solve for callers that hold the system in ordinary host memory:
  * copies rowptr/col/val/b/x to the device, solves on a library context, and
  * copies x back.  The copies are part of the call.
@@ -481,6 +517,8 @@ APCG_API apcg_status apcg_ir_plan_create(apcg_ctx ctx, apcg_mat A64, apcg_mat A3
 /* Solve A x = b (x holds x0 on entry).  Blocks once per correction to read two norms. */
 APCG_API apcg_status apcg_ir_plan_solve(apcg_ir_plan plan, apcg_vec b, apcg_vec x, apcg_ir_result* res);
 APCG_API apcg_status apcg_ir_plan_destroy(apcg_ir_plan plan);
+/* The sliced-ELL copy the plan's SpMVs read (see apcg_cg_plan_layout; the float32 and float64 copies share it). */
+APCG_API apcg_status apcg_ir_plan_layout(apcg_ir_plan plan, apcg_plan_layout* out);
 APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
                                    const apcg_ir_opts* opts, apcg_ir_result* res);
 
@@ -623,6 +661,8 @@ APCG_API apcg_status apcg_tfqmr_plan_create(apcg_ctx ctx, apcg_mat A, const apcg
 /* Solve with a plan; blocks until the solve ends. */
 APCG_API apcg_status apcg_tfqmr_plan_solve(apcg_tfqmr_plan plan, apcg_vec b, apcg_vec x, apcg_cg_result* res);
 APCG_API apcg_status apcg_tfqmr_plan_destroy(apcg_tfqmr_plan plan);
+/* The sliced-ELL copy the plan's SpMV reads (see apcg_cg_plan_layout). */
+APCG_API apcg_status apcg_tfqmr_plan_layout(apcg_tfqmr_plan plan, apcg_plan_layout* out);
 /* One-shot form of create + solve + destroy. */
 APCG_API apcg_status apcg_tfqmr_solve(apcg_ctx ctx, apcg_mat A, apcg_vec b, apcg_vec x, const apcg_cg_opts* opts,
                                       apcg_cg_result* res);

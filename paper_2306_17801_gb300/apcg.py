@@ -129,6 +129,17 @@ class IrResult(C.Structure):
         }
 
 
+COL_FORMATS = {-1: "none", 0: "index", 1: "offset16", 2: "pattern"}
+
+
+class PlanLayout(C.Structure):
+    _fields_ = [("col_format", C.c_int32), ("group", C.c_int32), ("nslices", C.c_int64), ("padded", C.c_int64)]
+
+    def as_dict(self):
+        return {"col_format": COL_FORMATS.get(int(self.col_format), int(self.col_format)), "group": int(self.group),
+                "nslices": int(self.nslices), "padded": int(self.padded)}
+
+
 class ExprTerm(C.Structure):
     _fields_ = [("op", C.c_int32), ("pad", C.c_int32), ("s", C.c_void_p), ("c", C.c_double)]
 
@@ -216,12 +227,14 @@ PROTOS = {
     "apcg_cg_plan_result": [P, C.POINTER(CgResult)],
     "apcg_cg_plan_destroy": [P],
     "apcg_cg_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
+    "apcg_cg_plan_layout": [P, C.POINTER(PlanLayout)],
     "apcg_cg_solve_host": [i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
     "apcg_cg_solve_noalloc": [P, i32, i64, P, P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
     "apcg_ir_opts_default": [C.POINTER(IrOpts)],
     "apcg_ir_plan_create": [P, P, P, C.POINTER(IrOpts), PP],
     "apcg_ir_plan_solve": [P, P, P, C.POINTER(IrResult)],
     "apcg_ir_plan_destroy": [P],
+    "apcg_ir_plan_layout": [P, C.POINTER(PlanLayout)],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
     "apcg_expr_create": [P, i32, PP],
     "apcg_expr_destroy": [P],
@@ -237,6 +250,7 @@ PROTOS = {
     "apcg_tfqmr_plan_create": [P, P, C.POINTER(CgOpts), PP],
     "apcg_tfqmr_plan_solve": [P, P, P, C.POINTER(CgResult)],
     "apcg_tfqmr_plan_destroy": [P],
+    "apcg_tfqmr_plan_layout": [P, C.POINTER(PlanLayout)],
     "apcg_tfqmr_solve": [P, P, P, P, C.POINTER(CgOpts), C.POINTER(CgResult)],
     "apcg_batch_plan_create": [P, i32, P, P, P, P, C.POINTER(CgOpts), PP],
     "apcg_batch_ir_plan_create": [P, i32, P, P, P, P, P, C.POINTER(IrOpts), PP],
@@ -458,6 +472,13 @@ def cg_plan_solve(plan, b, x) -> dict:
     res = CgResult()
     call("apcg_cg_plan_solve", C.c_void_p(plan), C.c_void_p(b), C.c_void_p(x), C.byref(res))
     return res.as_dict()
+
+
+def plan_layout(plan, kind: str = "cg") -> dict:
+    """The sliced-ELL copy a plan's SpMV reads (kind: "cg", "tfqmr" or "ir")."""
+    out = PlanLayout()
+    call(f"apcg_{kind}_plan_layout", C.c_void_p(plan), C.byref(out))
+    return out.as_dict()
 
 
 def cg_plan_profile(plan, b, x, iters: int) -> list[float]:

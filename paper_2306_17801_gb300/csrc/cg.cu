@@ -38,6 +38,7 @@ struct apcg_cg_plan_s {
   apcg_id id = 0;
   bool pending = false;
   int64_t last_launches = 0;
+  int64_t padded = 0;  // stored entries of the sliced-ELL copy
   // whole-solve cluster mode
   apcg::ClusterShape shape;
   apcg::SysDesc* sys = nullptr;
@@ -314,9 +315,11 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
   const size_t nst = up(sizeof(CgState));
   const size_t nh = up(sizeof(double) * (size_t)(c.hist_len > 0 ? c.hist_len : 1));
   const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
-  // column indices as 16-bit offsets from the row where they fit (2 bytes per entry less in every SpMV)
-  const size_t colw = L.d16 ? sizeof(int16_t) : sizeof(int32_t);
-  const size_t nsell = need_sell ? up(sizeof(int32_t) * ((size_t)L.nslices + 1)) + up(colw * (size_t)L.padded) +
+  // columns: one list of offsets per slice where the slices' rows share them (no column stream), else
+  // 16-bit offsets from the row where they fit (2 bytes per entry less in every SpMV), else 32-bit indices
+  const size_t ncolb = L.pattern ? sizeof(int32_t) * (size_t)(L.padded / 32)
+                                 : (L.d16 ? sizeof(int16_t) : sizeof(int32_t)) * (size_t)L.padded;
+  const size_t nsell = need_sell ? up(sizeof(int32_t) * ((size_t)L.nslices + 1)) + up(ncolb) +
                                        up(sizeof(double) * (size_t)L.padded)
                                  : 0;
   const size_t total = 5 * nv + npart + nst + 2 * nh + nsysb + nsell;
@@ -341,21 +344,24 @@ apcg_status cg_plan_create(apcg_ctx ctx, apcg_mat A, const apcg_stencil_s* S, co
     char* q = tail + nsysb;
     int32_t* sptr = reinterpret_cast<int32_t*>(q);
     q += up(sizeof(int32_t) * ((size_t)L.nslices + 1));
-    int32_t* scol = L.d16 ? nullptr : reinterpret_cast<int32_t*>(q);
+    int32_t* scol = (L.pattern || L.d16) ? nullptr : reinterpret_cast<int32_t*>(q);
     int16_t* sdcol = L.d16 ? reinterpret_cast<int16_t*>(q) : nullptr;
-    q += up(colw * (size_t)L.padded);
+    int32_t* spat = L.pattern ? reinterpret_cast<int32_t*>(q) : nullptr;
+    q += up(ncolb);
     double* sval = reinterpret_cast<double*>(q);
     APCG_CUDA(cudaMemcpyAsync(sptr, L.d_sptr, sizeof(int32_t) * ((size_t)L.nslices + 1), cudaMemcpyDeviceToDevice,
                               ctx->stream));
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
-                                       scol, sdcol, sval));
+                                       scol, sdcol, spat, sval));
     c.A.n = c.n;
     c.A.nslices = L.nslices;
     c.A.sptr = sptr;
     c.A.col = scol;
     c.A.dcol = sdcol;
+    c.A.poff = spat;
     c.A.val = sval;
     c.A.long_rows = L.group;  // the float64 SpMV's group size (K1 and the set-up kernel)
+    P->padded = L.padded;
     core_configure(c, A->nnz, ctx_num_sms(ctx));  // the SpMV kernel instance depends on the row length
   }
   SysDesc d0{};
@@ -467,6 +473,13 @@ apcg_status apcg_cg_plan_solve_async(apcg_cg_plan P, apcg_vec b, apcg_vec x) { r
 apcg_status apcg_cg_plan_result(apcg_cg_plan P, apcg_cg_result* res) { return cg_plan_finish(P, res); }
 
 apcg_status apcg_cg_plan_destroy(apcg_cg_plan P) { return cg_plan_destroy(P); }
+
+apcg_status apcg_cg_plan_layout(apcg_cg_plan P, apcg_plan_layout* out) {
+  APCG_CHECK(P && out, "plan or out is NULL");
+  const auto& A = P->core.A;
+  describe_layout(A.sptr != nullptr, dev::col_format(A), A.long_rows, A.nslices, P->padded, out);
+  return APCG_OK;
+}
 
 apcg_status apcg_cg_plan_profile(apcg_cg_plan P, apcg_vec b, apcg_vec x, int32_t iters, float* ms) {
   APCG_TRY(check_solve_args(P, b, x));

@@ -129,11 +129,11 @@ __device__ __forceinline__ void setup_body(const Args<double>& a, const double* 
   }
 }
 
-template <bool LONG, bool D16>
+template <bool LONG, int CF>
 __global__ void __launch_bounds__(kThreads) setup_kernel(Args<double> a, const double* __restrict__ b, double rtol,
                                                          double atol, int32_t max_it, int32_t k, int32_t hist_len) {
   setup_body(a, b, rtol, atol, max_it, k, hist_len,
-             [&](auto epi) { dev::sell_spmv<false, LONG, double, 8, D16>(a.A, a.x, epi); });
+             [&](auto epi) { dev::sell_spmv<false, LONG, double, 8, CF>(a.A, a.x, epi); });
 }
 
 // The stencil operator travels as its own parameter (not in Args, which every
@@ -163,13 +163,13 @@ __device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma) {
   }
 }
 
-// K1 (G: group size of the long-row path; D16: 16-bit column offsets)
-template <bool HOST, bool LONG, class T, int G = 8, bool D16 = false>
+// K1 (G: group size of the long-row path; CF: column format, dev::ColFormat)
+template <bool HOST, bool LONG, class T, int G = 8, int CF = dev::kColIndex>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   if (!HOST && read_done(a.st)) return;
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
-  dev::sell_spmv<true, LONG, T, G, D16>(a.A, a.p, [&](int32_t i, T s, T p_i) {
+  dev::sell_spmv<true, LONG, T, G, CF>(a.A, a.p, [&](int32_t i, T s, T p_i) {
                                      a.w[i] = s;
                                      v[0] = fma(p_i, s, v[0]);
                                    });
@@ -385,23 +385,25 @@ apcg_status k1_stencil_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream
 // 5..9 (csr_layout); the float32 inner solves of the refinement keep 0 or 8: they are bound by HBM, not by
 // wasted FMA slots, and larger groups cost them occupancy (refinement at 160^3 with groups of 9: 110.2
 // against 107.3 ms).
-template <bool HOST, class T, bool D16>
+template <bool HOST, class T, int CF>
 void* k1_instance_d(const CgCore<T>& c) {
   if constexpr (std::is_same<T, double>::value) {
     switch (c.A.long_rows) {
-      case 5: return (void*)k1_kernel<HOST, true, T, 5, D16>;
-      case 6: return (void*)k1_kernel<HOST, true, T, 6, D16>;
-      case 7: return (void*)k1_kernel<HOST, true, T, 7, D16>;
-      case 9: return (void*)k1_kernel<HOST, true, T, 9, D16>;
+      case 5: return (void*)k1_kernel<HOST, true, T, 5, CF>;
+      case 6: return (void*)k1_kernel<HOST, true, T, 6, CF>;
+      case 7: return (void*)k1_kernel<HOST, true, T, 7, CF>;
+      case 9: return (void*)k1_kernel<HOST, true, T, 9, CF>;
       default: break;
     }
   }
-  return c.A.long_rows ? (void*)k1_kernel<HOST, true, T, 8, D16> : (void*)k1_kernel<HOST, false, T, 8, D16>;
+  return c.A.long_rows ? (void*)k1_kernel<HOST, true, T, 8, CF> : (void*)k1_kernel<HOST, false, T, 8, CF>;
 }
 
 template <bool HOST, class T>
 void* k1_instance(const CgCore<T>& c) {
-  return c.A.dcol ? k1_instance_d<HOST, T, true>(c) : k1_instance_d<HOST, T, false>(c);
+  if (c.A.poff) return k1_instance_d<HOST, T, dev::kColPattern>(c);
+  if (c.A.dcol) return k1_instance_d<HOST, T, dev::kColOff16>(c);
+  return k1_instance_d<HOST, T, dev::kColIndex>(c);
 }
 
 template <bool HOST, class T>
@@ -513,15 +515,17 @@ apcg_status core_setup_f64(const CgCore<double>& c, const double* b, double* x, 
       case 27: setup_stencil_kernel<27><<<g, kThreads, 0, s>>>(a, c.S, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
       default: setup_stencil_kernel<0><<<g, kThreads, 0, s>>>(a, c.S, b, rtol, atol, c.max_it, c.k, c.hist_len); break;
     }
-  } else if (c.A.dcol) {
-    if (c.A.long_rows)
-      setup_kernel<true, true><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
-    else
-      setup_kernel<false, true><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
-  } else if (c.A.long_rows) {
-    setup_kernel<true, false><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
   } else {
-    setup_kernel<false, false><<<c.grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len);
+    const int g = c.grid_spmv;
+    const bool lr = c.A.long_rows != 0;
+#define APCG_SETUP(L, F) setup_kernel<L, F><<<g, kThreads, 0, s>>>(a, b, rtol, atol, c.max_it, c.k, c.hist_len)
+    if (c.A.poff)
+      lr ? APCG_SETUP(true, dev::kColPattern) : APCG_SETUP(false, dev::kColPattern);
+    else if (c.A.dcol)
+      lr ? APCG_SETUP(true, dev::kColOff16) : APCG_SETUP(false, dev::kColOff16);
+    else
+      lr ? APCG_SETUP(true, dev::kColIndex) : APCG_SETUP(false, dev::kColIndex);
+#undef APCG_SETUP
   }
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;

@@ -48,6 +48,7 @@ struct apcg_ir_plan_s {
   char* ws = nullptr;
   int grid_res = 1, grid_upd = 1;
   bool outer64 = false;
+  int64_t padded = 0;  // stored entries of the sliced-ELL copy
   void* host_state = nullptr;  // pinned: IrState followed by CgState
 };
 
@@ -101,17 +102,15 @@ apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cu
     return APCG_OK;
   }
   const bool lg = P->A32.long_rows != 0;
-  if (P->outer64) {
-    if (lg)
-      ir::residual_kernel<true, double><<<P->grid_res, kThreads, 0, s>>>(a, P->A64);
-    else
-      ir::residual_kernel<false, double><<<P->grid_res, kThreads, 0, s>>>(a, P->A64);
-  } else {
-    if (lg)
-      ir::residual_kernel<true, float><<<P->grid_res, kThreads, 0, s>>>(a, P->A32);
-    else
-      ir::residual_kernel<false, float><<<P->grid_res, kThreads, 0, s>>>(a, P->A32);
-  }
+  const bool pat = P->A32.poff != nullptr;
+#define APCG_RES(L, TV, V) \
+  (pat ? ir::residual_kernel<L, TV, dev::kColPattern><<<P->grid_res, kThreads, 0, s>>>(a, V) \
+       : ir::residual_kernel<L, TV, dev::kColIndex><<<P->grid_res, kThreads, 0, s>>>(a, V))
+  if (P->outer64)
+    lg ? APCG_RES(true, double, P->A64) : APCG_RES(false, double, P->A64);
+  else
+    lg ? APCG_RES(true, float, P->A32) : APCG_RES(false, float, P->A32);
+#undef APCG_RES
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -175,15 +174,16 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   P->grid_upd = std::max(1, std::min(sms * 8, (int)((P->n / 4 + kThreads - 1) / kThreads)));
   SellLayout L;
   APCG_TRY(csr_layout(ctx, &S, true, &L));
-  // 32-bit column indices here even where 16-bit offsets would fit: the float32 inner SpMV is bound by HBM at
-  // six blocks per SM, and the offset form's extra registers cost it one (160^3 27-point refinement: 108.8
-  // against 107.8 ms).
+  // Columns: per-slice offset lists where the slices' rows share them (no column stream: 4 of the float32
+  // SpMV's 8 bytes per entry), else 32-bit indices even where 16-bit offsets would fit: the float32 inner SpMV
+  // is bound by HBM at six blocks per SM, and the offset form's extra registers cost it one (160^3 27-point
+  // refinement: 108.8 against 107.8 ms).
   // Workspace: sliced-ELL (sptr, col, float32 values, float64 values if A64), dinv32, r, p, w, z, d,
   // partials and states.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(float) * (size_t)(P->n > 0 ? P->n : 1));
   const size_t nsptr = up(sizeof(int32_t) * ((size_t)L.nslices + 1));
-  const size_t ncol = up(sizeof(int32_t) * (size_t)std::max<int64_t>(L.padded, 1));
+  const size_t ncol = up(sizeof(int32_t) * (size_t)std::max<int64_t>(L.pattern ? L.padded / 32 : L.padded, 1));
   const size_t nv32 = up(sizeof(float) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nv64 = A64 ? up(sizeof(double) * (size_t)std::max<int64_t>(L.padded, 1)) : 0;
   const size_t nip = up(sizeof(float) * dev::kMaxPartials * 3);
@@ -196,7 +196,8 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   char* q = ws;
   int32_t* sptr = reinterpret_cast<int32_t*>(q);
   q += nsptr;
-  int32_t* scol = reinterpret_cast<int32_t*>(q);
+  int32_t* scol = L.pattern ? nullptr : reinterpret_cast<int32_t*>(q);
+  int32_t* spat = L.pattern ? reinterpret_cast<int32_t*>(q) : nullptr;
   q += ncol;
   float* sval32 = reinterpret_cast<float*>(q);
   q += nv32;
@@ -227,25 +228,28 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
                             ctx->stream));
   if (A32)
     APCG_TRY(sell_fill<float, float>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const float*>(A32->val),
-                                     scol, nullptr, sval32));
+                                     scol, nullptr, spat, sval32));
   else
     APCG_TRY(sell_fill<double, float>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const double*>(A64->val),
-                                      scol, nullptr, sval32));
+                                      scol, nullptr, spat, sval32));
   if (A64)
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, S.rowptr, S.col, static_cast<const double*>(A64->val),
-                                       nullptr, nullptr, sval64));
+                                       nullptr, nullptr, nullptr, sval64));
   P->A32.n = P->A64.n = P->n;
   P->A32.nslices = L.nslices;
   P->A32.sptr = sptr;
   P->A32.col = scol;
+  P->A32.poff = spat;
   P->A32.val = sval32;
   if (A64) {
     P->A64.nslices = L.nslices;
     P->A64.sptr = sptr;
     P->A64.col = scol;
+    P->A64.poff = spat;
     P->A64.val = sval64;
   }
   P->A32.long_rows = P->A64.long_rows = L.long_rows;
+  P->padded = L.padded;
   c.A = P->A32;
   core_configure(c, S.nnz, sms);  // the SpMV kernel instance depends on the row length
   P->grid_res = c.grid_spmv;
@@ -425,6 +429,14 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
   count_kernels(launches);
   apcg_status st2 = op.finish();
   return st != APCG_OK ? st : st2;
+}
+
+apcg_status apcg_ir_plan_layout(apcg_ir_plan P, apcg_plan_layout* out) {
+  APCG_CHECK(P && out, "plan or out is NULL");
+  // the float32 SpMV's group: 8 where the rows are long, else one entry at a time
+  describe_layout(P->A32.sptr != nullptr, dev::col_format(P->A32), P->A32.long_rows ? 8 : 0, P->A32.nslices,
+                  P->padded, out);
+  return APCG_OK;
 }
 
 apcg_status apcg_ir_plan_destroy(apcg_ir_plan P) {

@@ -102,9 +102,9 @@ __device__ __forceinline__ void residual_body(const ResidualArgs& a, Spmv spmv) 
   }
 }
 
-template <bool LONG, class TV>
+template <bool LONG, class TV, int CF>
 __global__ void __launch_bounds__(kThreads) residual_kernel(ResidualArgs a, dev::SellView<TV> A) {
-  residual_body(a, [&](auto epi) { dev::sell_spmv<false, LONG, double>(A, a.x, epi); });
+  residual_body(a, [&](auto epi) { dev::sell_spmv<false, LONG, double, 8, CF>(A, a.x, epi); });
 }
 
 // The same on a stencil operator (float64 weights).

@@ -17,10 +17,27 @@
 
 #include <cstdint>
 
+#include "apcg.h"
 #include "kernels_common.cuh"
 
 namespace apcg {
 namespace dev {
+
+// How the column of a stored entry is found (the SpMV's CF argument):
+//   kColIndex:   a 32-bit index per entry (A.col);
+//   kColOff16:   a 16-bit offset from the row per entry (A.dcol), for
+//                matrices whose entries all lie within 32767 of the diagonal;
+//   kColPattern: one list of offsets from the row per slice (A.poff), shared
+//                by its 32 rows.  Entry k of every row of slice s has the
+//                column row + poff[sptr[s] / 32 + k]; a row without that
+//                offset stores the value 0 there.  Built where each row's
+//                columns increase and the union of a slice's offsets is
+//                (nearly) as short as its longest row -- stencil matrices,
+//                whose rows differ only where the grid ends.  No column bytes
+//                stream from memory at all.
+enum ColFormat : int { kColIndex = 0, kColOff16 = 1, kColPattern = 2 };
+static_assert(kColIndex == APCG_COLS_INDEX && kColOff16 == APCG_COLS_OFFSET16 && kColPattern == APCG_COLS_PATTERN,
+              "the column formats are reported by their APCG_COLS_* values");
 
 template <class TV>
 struct SellView {
@@ -28,10 +45,29 @@ struct SellView {
   int32_t nslices = 0;  // ceil(n / 32)
   const int32_t* __restrict__ sptr = nullptr;  // [nslices + 1] entry offsets (multiples of 32)
   const int32_t* __restrict__ col = nullptr;   // [sptr[nslices]] column indices, or
-  const int16_t* __restrict__ dcol = nullptr;  // [sptr[nslices]] column - row (the D16 instances)
+  const int16_t* __restrict__ dcol = nullptr;  // [sptr[nslices]] column - row (kColOff16), or
+  const int32_t* __restrict__ poff = nullptr;  // [sptr[nslices] / 32] per-slice column offsets (kColPattern)
   const TV* __restrict__ val = nullptr;        // [sptr[nslices]]
   int32_t long_rows = 0;  // 0: one entry at a time; else the group size G of the grouped path (8 or 9)
 };
+
+template <class TV>
+__host__ __device__ inline int col_format(const SellView<TV>& A) {
+  return A.poff ? kColPattern : A.dcol ? kColOff16 : kColIndex;
+}
+
+// Column of entry k of this lane's row in the given format (see ColFormat).
+template <int CF>
+__device__ __forceinline__ int32_t sell_column(const int32_t* cp, const int16_t* dp, const int32_t* op, int32_t k,
+                                               int32_t row, int32_t last) {
+  if constexpr (CF == kColIndex) {
+    return ld_stream(cp + 32 * k);
+  } else if constexpr (CF == kColOff16) {
+    return row + (int32_t)ld_stream(dp + 32 * k);
+  } else {
+    return min(max(row + __ldg(op + k), 0), last);
+  }
+}
 
 // Apply epi(row, (A x)[row], x[row]) for every row; warps of the grid take
 // slices in a grid-stride loop.  Values TV are widened to T, the type of x
@@ -43,11 +79,12 @@ struct SellView {
 // warp instruction costs pipe time, so the plan picks the G that wastes the
 // fewest (27-point rows: G = 9, three whole groups, against 32 slots for 27
 // entries with G = 8; measured 228 against 256 us per launch at 160^3).
-// D16: the column of an entry is read as a 16-bit offset from its row
-// (A.dcol) instead of a 32-bit index (A.col): 2 bytes per entry less, for
-// matrices whose entries all lie within 32767 of the diagonal (the plan
-// checks).  The sums are the same.
-template <bool OWN_X, bool LONG, class T, int G = 8, bool D16 = false, class TV, class Epi>
+// CF selects the column format (ColFormat).  The sums are the same in all
+// three: each row adds its entries in its CSR order, plus exact zeros.  In the
+// pattern format an offset that a row lacks may point outside [0, n) (at the
+// edges of the grid, or past the last row); its column is clamped into range,
+// where it multiplies the stored 0.
+template <bool OWN_X, bool LONG, class T, int G = 8, int CF = kColIndex, class TV, class Epi>
 __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __restrict__ x, Epi epi) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -66,8 +103,10 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
     const int32_t row = (int32_t)(s * 32 + lane);
     T x_own = T(0);
     if (OWN_X && row < A.n) x_own = ld_ro(x + row);
-    const int32_t* cp = D16 ? nullptr : A.col + base + lane;
-    const int16_t* dp = D16 ? A.dcol + base + lane : nullptr;
+    const int32_t* cp = CF == kColIndex ? A.col + base + lane : nullptr;
+    const int16_t* dp = CF == kColOff16 ? A.dcol + base + lane : nullptr;
+    const int32_t* op = CF == kColPattern ? A.poff + (base >> 5) : nullptr;
+    const int32_t last = A.n - 1;
     const TV* vp = A.val + base + lane;
     const int32_t width = (end - base) >> 5;
     T acc = T(0);
@@ -84,7 +123,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
 #pragma unroll
         for (int g = 0; g < G; ++g) {
           const bool ok = k + g < width;
-          j[g] = ok ? (D16 ? row + (int32_t)ld_stream(dp + 32 * (k + g)) : ld_stream(cp + 32 * (k + g))) : 0;
+          j[g] = ok ? sell_column<CF>(cp, dp, op, k + g, row, last) : 0;
           a[g] = ok ? ld_stream(vp + 32 * (k + g)) : TV(0);
         }
 #pragma unroll
@@ -97,7 +136,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
       // Short rows (5- and 7-point stencils): one entry at a time (measured
       // faster: fewer registers, more resident warps).
       for (int32_t k = 0; k < width; ++k) {
-        const int32_t j = D16 ? row + (int32_t)ld_stream(dp + 32 * k) : ld_stream(cp + 32 * k);
+        const int32_t j = sell_column<CF>(cp, dp, op, k, row, last);
         const TV a = ld_stream(vp + 32 * k);
         acc = fma((T)a, ld_ro(x + j), acc);
       }

@@ -115,12 +115,12 @@ __device__ __forceinline__ bool quasi_update(TqState* st, double ww) {
 
 // S1: r0 = D^-1 (b - A x0);  u = w = r* = r0;  d = 0;  ||r0||^2, ||D^-1 b||^2;
 // tau = ||r0||, rho = (r*, r0), the tolerance and the initial test.
-template <bool LONG, bool D16>
+template <bool LONG, int CF>
 __global__ void __launch_bounds__(kThreads) s1_kernel(TqArgs a, const double* __restrict__ b, double rtol,
                                                       double atol, int32_t max_it, int32_t k, int32_t hist_len) {
   __shared__ double red[2 * kThreads];
   double v[2] = {0.0, 0.0};
-  dev::sell_spmv<false, LONG, double, 8, D16>(a.A, a.x, [&](int32_t i, double ax, double) {
+  dev::sell_spmv<false, LONG, double, 8, CF>(a.A, a.x, [&](int32_t i, double ax, double) {
                                            const double di = __ldg(a.dinv + i);
                                            const double bi = __ldg(b + i);
                                            const double ri = di * (bi - ax);
@@ -155,12 +155,12 @@ __global__ void __launch_bounds__(kThreads) s1_kernel(TqArgs a, const double* __
 }
 
 // S2: p = M u;  v = p;  sigma = (v, r*);  alpha = rho / sigma (device mode).
-template <bool HOST, bool LONG, bool D16>
+template <bool HOST, bool LONG, int CF>
 __global__ void __launch_bounds__(kThreads) s2_kernel(TqArgs a) {
   if (!HOST && read_done(a.st)) return;
   __shared__ double red[kThreads];
   double v[1] = {0.0};
-  dev::sell_spmv<false, LONG, double, 8, D16>(a.A, a.u, [&](int32_t i, double au, double) {
+  dev::sell_spmv<false, LONG, double, 8, CF>(a.A, a.u, [&](int32_t i, double au, double) {
                                            const double pi = __ldg(a.dinv + i) * au;
                                            a.p[i] = pi;
                                            a.v[i] = pi;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 4) t1_kernel(TqArgs a, HostScalars h
 // per SM, a few bytes of spill): the extra resident warps hide more of the
 // gathers' latency (128^3 7-point: 173 against 180 us per iteration at 48
 // registers and five blocks).  T3 runs on its own grid at its own occupancy.
-template <bool HOST, int G, bool D16>
+template <bool HOST, int G, int CF>
 __global__ void __launch_bounds__(kThreads, G == 0 ? 6 : 4) t2_kernel(TqArgs a, HostScalars h,
                                                                    cudaGraphConditionalHandle cond, int32_t use_cond) {
   if (!HOST && read_done(a.st)) {
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, G == 0 ? 6 : 4) t2_kernel(TqArgs a, 
   const double ex = HOST ? h.eta_x : a.st->eta_x;
   __shared__ double red[2 * kThreads];
   double v[2] = {0.0, 0.0};
-  dev::sell_spmv<true, (G > 0), double, (G > 0 ? G : 8), D16>(a.A, a.u2, [&](int32_t i, double au2, double u2i) {
+  dev::sell_spmv<true, (G > 0), double, (G > 0 ? G : 8), CF>(a.A, a.u2, [&](int32_t i, double au2, double u2i) {
                                           const double qi = __ldg(a.dinv + i) * au2;
                                           double di = a.d[i];
                                           if (pend) a.x[i] = fma(ex, di, a.x[i]);
@@ -321,13 +321,13 @@ __global__ void __launch_bounds__(kThreads, G == 0 ? 6 : 4) t2_kernel(TqArgs a, 
 
 // T3, the direction update: u = w + beta u2;  p = M w + beta q (= M u);
 // v = p + beta (q + beta v);  sigma = (v, r*) and alpha in the last block.
-template <bool HOST, int G, bool D16>
+template <bool HOST, int G, int CF>
 __global__ void __launch_bounds__(kThreads) t3_kernel(TqArgs a, HostScalars h) {
   if (!HOST && read_done(a.st)) return;
   const double beta = HOST ? h.beta : a.st->beta;
   __shared__ double red[kThreads];
   double v[1] = {0.0};
-  dev::sell_spmv<true, (G > 0), double, (G > 0 ? G : 8), D16>(a.A, a.w, [&](int32_t i, double aw, double wi) {
+  dev::sell_spmv<true, (G > 0), double, (G > 0 ? G : 8), CF>(a.A, a.w, [&](int32_t i, double aw, double wi) {
                                           const double mwi = __ldg(a.dinv + i) * aw;
                                           const double qi = a.q[i];
                                           a.u[i] = fma(beta, a.u2[i], wi);
@@ -404,6 +404,7 @@ struct apcg_tfqmr_plan_s {
   int grid_spmv = 1, grid_vec = 1, grid_t3 = 1;  // t3 takes fewer registers than t2: its own persistent grid
   bool long_rows = false;  // the set-up kernels' SpMV path
   int group = 0;           // the iteration kernels' SpMV group size (0: one entry at a time)
+  int64_t padded = 0;      // stored entries of the sliced-ELL copy
   char* ws = nullptr;
   apcg::tq::TqState* st_host = nullptr;  // pinned mirror of the state block
   apcg_id id = 0;
@@ -435,12 +436,15 @@ TqArgs args_for(Plan P, double* x) {
 apcg_status launch_s1(Plan P, double* x, const double* b, cudaStream_t s) {
   const TqArgs a = args_for(P, x);
   const double rtol = P->opts.rtol, atol = P->opts.atol;
-  const bool d = P->a.A.dcol != nullptr;
-#define APCG_S1(L, D) s1_kernel<L, D><<<P->grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, P->max_it, P->k, P->hist_len)
+  const int cf = dev::col_format(P->a.A);
+#define APCG_S1(L, F) s1_kernel<L, F><<<P->grid_spmv, kThreads, 0, s>>>(a, b, rtol, atol, P->max_it, P->k, P->hist_len)
+#define APCG_S1F(L) \
+  (cf == dev::kColPattern ? APCG_S1(L, dev::kColPattern) : cf == dev::kColOff16 ? APCG_S1(L, dev::kColOff16) : APCG_S1(L, dev::kColIndex))
   if (P->long_rows)
-    d ? APCG_S1(true, true) : APCG_S1(true, false);
+    APCG_S1F(true);
   else
-    d ? APCG_S1(false, true) : APCG_S1(false, false);
+    APCG_S1F(false);
+#undef APCG_S1F
 #undef APCG_S1
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
@@ -448,19 +452,15 @@ apcg_status launch_s1(Plan P, double* x, const double* b, cudaStream_t s) {
 
 apcg_status launch_s2(Plan P, double* x, cudaStream_t s, bool host) {
   const TqArgs a = args_for(P, x);
-  const bool d = P->a.A.dcol != nullptr;
-#define APCG_S2(H, L, D) s2_kernel<H, L, D><<<P->grid_spmv, kThreads, 0, s>>>(a)
-  if (host) {
-    if (P->long_rows)
-      d ? APCG_S2(true, true, true) : APCG_S2(true, true, false);
-    else
-      d ? APCG_S2(true, false, true) : APCG_S2(true, false, false);
-  } else {
-    if (P->long_rows)
-      d ? APCG_S2(false, true, true) : APCG_S2(false, true, false);
-    else
-      d ? APCG_S2(false, false, true) : APCG_S2(false, false, false);
-  }
+  const int cf = dev::col_format(P->a.A);
+#define APCG_S2(H, L, F) s2_kernel<H, L, F><<<P->grid_spmv, kThreads, 0, s>>>(a)
+#define APCG_S2F(H, L) \
+  (cf == dev::kColPattern ? APCG_S2(H, L, dev::kColPattern) : cf == dev::kColOff16 ? APCG_S2(H, L, dev::kColOff16) : APCG_S2(H, L, dev::kColIndex))
+  if (host)
+    P->long_rows ? APCG_S2F(true, true) : APCG_S2F(true, false);
+  else
+    P->long_rows ? APCG_S2F(false, true) : APCG_S2F(false, false);
+#undef APCG_S2F
 #undef APCG_S2
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
@@ -477,43 +477,49 @@ apcg_status launch_t1(Plan P, double* x, cudaStream_t s, bool host, const HostSc
 }
 
 // The instance of T2 or T3 for the plan's group size and column format.
-template <bool HOST, bool D16>
+template <bool HOST, int CF>
 void* t2_instance(int g) {
   switch (g) {
-    case 5: return (void*)t2_kernel<HOST, 5, D16>;
-    case 6: return (void*)t2_kernel<HOST, 6, D16>;
-    case 7: return (void*)t2_kernel<HOST, 7, D16>;
-    case 8: return (void*)t2_kernel<HOST, 8, D16>;
-    case 9: return (void*)t2_kernel<HOST, 9, D16>;
-    default: return (void*)t2_kernel<HOST, 0, D16>;
+    case 5: return (void*)t2_kernel<HOST, 5, CF>;
+    case 6: return (void*)t2_kernel<HOST, 6, CF>;
+    case 7: return (void*)t2_kernel<HOST, 7, CF>;
+    case 8: return (void*)t2_kernel<HOST, 8, CF>;
+    case 9: return (void*)t2_kernel<HOST, 9, CF>;
+    default: return (void*)t2_kernel<HOST, 0, CF>;
   }
 }
-template <bool HOST, bool D16>
+template <bool HOST, int CF>
 void* t3_instance(int g) {
   switch (g) {
-    case 5: return (void*)t3_kernel<HOST, 5, D16>;
-    case 6: return (void*)t3_kernel<HOST, 6, D16>;
-    case 7: return (void*)t3_kernel<HOST, 7, D16>;
-    case 8: return (void*)t3_kernel<HOST, 8, D16>;
-    case 9: return (void*)t3_kernel<HOST, 9, D16>;
-    default: return (void*)t3_kernel<HOST, 0, D16>;
+    case 5: return (void*)t3_kernel<HOST, 5, CF>;
+    case 6: return (void*)t3_kernel<HOST, 6, CF>;
+    case 7: return (void*)t3_kernel<HOST, 7, CF>;
+    case 8: return (void*)t3_kernel<HOST, 8, CF>;
+    case 9: return (void*)t3_kernel<HOST, 9, CF>;
+    default: return (void*)t3_kernel<HOST, 0, CF>;
   }
 }
-void* t2_for(bool host, bool d16, int g) {
-  return host ? (d16 ? t2_instance<true, true>(g) : t2_instance<true, false>(g))
-              : (d16 ? t2_instance<false, true>(g) : t2_instance<false, false>(g));
+template <bool HOST>
+void* t2_for_cf(int cf, int g) {
+  return cf == dev::kColPattern ? t2_instance<HOST, dev::kColPattern>(g)
+         : cf == dev::kColOff16 ? t2_instance<HOST, dev::kColOff16>(g)
+                                : t2_instance<HOST, dev::kColIndex>(g);
 }
-void* t3_for(bool host, bool d16, int g) {
-  return host ? (d16 ? t3_instance<true, true>(g) : t3_instance<true, false>(g))
-              : (d16 ? t3_instance<false, true>(g) : t3_instance<false, false>(g));
+template <bool HOST>
+void* t3_for_cf(int cf, int g) {
+  return cf == dev::kColPattern ? t3_instance<HOST, dev::kColPattern>(g)
+         : cf == dev::kColOff16 ? t3_instance<HOST, dev::kColOff16>(g)
+                                : t3_instance<HOST, dev::kColIndex>(g);
 }
+void* t2_for(bool host, int cf, int g) { return host ? t2_for_cf<true>(cf, g) : t2_for_cf<false>(cf, g); }
+void* t3_for(bool host, int cf, int g) { return host ? t3_for_cf<true>(cf, g) : t3_for_cf<false>(cf, g); }
 
 apcg_status launch_t2(Plan P, double* x, cudaStream_t s, bool host, const HostScalars& h,
                       cudaGraphConditionalHandle cond, int32_t use_cond) {
   TqArgs a = args_for(P, x);
   HostScalars hh = h;
   void* args[] = {&a, &hh, &cond, &use_cond};
-  void* k = t2_for(host, P->a.A.dcol != nullptr, P->group);
+  void* k = t2_for(host, dev::col_format(P->a.A), P->group);
   APCG_CUDA(cudaLaunchKernel(k, dim3(P->grid_spmv), dim3(kThreads), args, 0, s));
   return APCG_OK;
 }
@@ -522,7 +528,7 @@ apcg_status launch_t3(Plan P, double* x, cudaStream_t s, bool host, const HostSc
   TqArgs a = args_for(P, x);
   HostScalars hh = h;
   void* args[] = {&a, &hh};
-  void* k = t3_for(host, P->a.A.dcol != nullptr, P->group);
+  void* k = t3_for(host, dev::col_format(P->a.A), P->group);
   APCG_CUDA(cudaLaunchKernel(k, dim3(P->grid_t3), dim3(kThreads), args, 0, s));
   return APCG_OK;
 }
@@ -849,9 +855,11 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   P->long_rows = L.long_rows != 0;
   P->group = L.group;
   const int64_t slices = ((int64_t)P->n + 31) / 32;
-  const bool d16 = L.d16 && P->mode != APCG_MODE_PERSISTENT;
-  P->grid_spmv = occupancy_grid(t2_for(false, d16, P->group), sms, (slices + 7) / 8);
-  P->grid_t3 = occupancy_grid(t3_for(false, d16, P->group), sms, (slices + 7) / 8);
+  const bool sell = P->mode != APCG_MODE_PERSISTENT;
+  const bool pat = L.pattern && sell, d16 = L.d16 && sell;
+  const int cf = pat ? dev::kColPattern : d16 ? dev::kColOff16 : dev::kColIndex;
+  P->grid_spmv = occupancy_grid(t2_for(false, cf, P->group), sms, (slices + 7) / 8);
+  P->grid_t3 = occupancy_grid(t3_for(false, cf, P->group), sms, (slices + 7) / 8);
   P->grid_vec = occupancy_grid(t1_kernel<false>, sms, ((int64_t)P->n / 2 + kThreads - 1) / kThreads);
   // Workspace: dinv, r*, u, u2, w, d, v, p, q; partials; state; histories; sliced-ELL copy.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -860,8 +868,10 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   const size_t nst = up(sizeof(TqState));
   const size_t nh = up(sizeof(double) * (size_t)(P->hist_len > 0 ? P->hist_len : 1));
   const size_t nsptr = up(sizeof(int32_t) * ((size_t)L.nslices + 1));
-  // column indices: 16-bit offsets from the row where they all fit, else 32-bit
-  const size_t ncol = up((d16 ? sizeof(int16_t) : sizeof(int32_t)) * (size_t)std::max<int64_t>(L.padded, 1));
+  // columns: per-slice offset lists where the slices' rows share them, else 16-bit offsets from the row
+  // where they all fit, else 32-bit indices
+  const size_t ncol = up(pat ? sizeof(int32_t) * (size_t)std::max<int64_t>(L.padded / 32, 1)
+                             : (d16 ? sizeof(int16_t) : sizeof(int32_t)) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nval = up(sizeof(double) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
   const size_t total = 9 * nv + npart + nst + 2 * nh + nsptr + ncol + nval + nsysb;
@@ -889,14 +899,15 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   APCG_CUDA(cudaMemsetAsync(q, 0, npart + nst + 2 * nh, ctx->stream));
   q += npart + nst + 2 * nh;
   int32_t* sptr = reinterpret_cast<int32_t*>(q);
-  int32_t* scol = d16 ? nullptr : reinterpret_cast<int32_t*>(q + nsptr);
+  int32_t* scol = (pat || d16) ? nullptr : reinterpret_cast<int32_t*>(q + nsptr);
   int16_t* sdcol = d16 ? reinterpret_cast<int16_t*>(q + nsptr) : nullptr;
+  int32_t* spat = pat ? reinterpret_cast<int32_t*>(q + nsptr) : nullptr;
   double* sval = reinterpret_cast<double*>(q + nsptr + ncol);
   if (P->mode != APCG_MODE_PERSISTENT) {
     APCG_CUDA(cudaMemcpyAsync(sptr, L.d_sptr, sizeof(int32_t) * ((size_t)L.nslices + 1), cudaMemcpyDeviceToDevice,
                               ctx->stream));
     APCG_TRY(sell_fill<double, double>(ctx->stream, L, sptr, A->rowptr, A->col, static_cast<const double*>(A->val),
-                                       scol, sdcol, sval));
+                                       scol, sdcol, spat, sval));
   }
   char* tail = q + nsptr + ncol + nval;
   P->sys = reinterpret_cast<SysDesc*>(tail);
@@ -907,11 +918,13 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   d0.n = P->n;
   APCG_CUDA(cudaMemcpyAsync(P->sys, &d0, sizeof(d0), cudaMemcpyHostToDevice, ctx->stream));
   APCG_CUDA(cudaMallocHost((void**)&P->sres_host, sizeof(SysResult)));
+  P->padded = L.padded;
   a.A.n = P->n;
   a.A.nslices = L.nslices;
   a.A.sptr = sptr;
   a.A.col = scol;
   a.A.dcol = sdcol;
+  a.A.poff = spat;
   a.A.val = sval;
   a.A.long_rows = L.long_rows;
   APCG_CUDA(cudaMallocHost((void**)&P->st_host, sizeof(TqState)));
@@ -978,6 +991,13 @@ apcg_status apcg_tfqmr_plan_solve(apcg_tfqmr_plan P, apcg_vec b, apcg_vec x, apc
 }
 
 apcg_status apcg_tfqmr_plan_destroy(apcg_tfqmr_plan P) { return tq::plan_destroy(P); }
+
+apcg_status apcg_tfqmr_plan_layout(apcg_tfqmr_plan P, apcg_plan_layout* out) {
+  APCG_CHECK(P && out, "plan or out is NULL");
+  const bool copy = P->mode != APCG_MODE_PERSISTENT && P->a.A.sptr != nullptr;
+  describe_layout(copy, dev::col_format(P->a.A), P->group, P->a.A.nslices, P->padded, out);
+  return APCG_OK;
+}
 
 apcg_status apcg_tfqmr_solve(apcg_ctx ctx, apcg_mat A, apcg_vec b, apcg_vec x, const apcg_cg_opts* opts,
                              apcg_cg_result* res) {
