@@ -382,9 +382,9 @@ apcg_status k1_stencil_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream
 }
 
 // The K1 instance for the plan's layout: one entry at a time, or groups of G.  The float64 plans choose G in
-// 5..9 (csr_layout); the float32 inner solves of the refinement keep 0 or 8: they are bound by HBM, not by
-// wasted FMA slots, and larger groups cost them occupancy (refinement at 160^3 with groups of 9: 110.2
-// against 107.3 ms).
+// 5..9 (csr_layout); the float32 inner solves of the refinement keep 0 or 8 with per-entry column indices:
+// they are bound by HBM, not by wasted FMA slots, and larger groups cost them occupancy (refinement at 160^3
+// with groups of 9: 110.2 against 107.3 ms).
 template <bool HOST, class T, int CF>
 void* k1_instance_d(const CgCore<T>& c) {
   if constexpr (std::is_same<T, double>::value) {
@@ -396,6 +396,10 @@ void* k1_instance_d(const CgCore<T>& c) {
       default: break;
     }
   }
+  // float32 with per-slice offset lists: 27-entry rows in three whole groups of 9 (no column loads, so the
+  // larger group costs no occupancy; 160^3 refinement 86.2 -> 81.6 ms)
+  if constexpr (CF == dev::kColPattern && std::is_same<T, float>::value)
+    if (c.A.long_rows == 9) return (void*)k1_kernel<HOST, true, T, 9, CF>;
   return c.A.long_rows ? (void*)k1_kernel<HOST, true, T, 8, CF> : (void*)k1_kernel<HOST, false, T, 8, CF>;
 }
 
