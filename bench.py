@@ -531,20 +531,30 @@ def bench_c3(args):
 
     plan = apcg.cg_plan_create(ctx, g["A"], apcg.cg_opts(rtol=1e-10, check_every=10, mode="async_graph", max_it=50000))
     ms64, r64 = timed(lambda: apcg.cg_plan_solve(plan, g["vb"], g["vx"]), max(1, args.steps // 3))
+    k64 = apcg.cg_plan_profile(plan, g["vb"], g["vx"], 5)  # after the timed solves: x is overwritten
+    lay64 = apcg.plan_layout(plan, "cg")
     apcg.call("apcg_cg_plan_destroy", V(plan))
     b_it64 = 12 * nnz + 4 * (n + 1) + 104 * n
+    b_k1_64 = 12 * nnz + 4 * (n + 1) + 16 * n
     out["fp64_pcg"] = {
         "ms_per_solve": ms64, "iters": r64["iters"], "us_per_iteration": 1e3 * ms64 / r64["iters"],
         "GBps_per_iteration": b_it64 / (1e-3 * ms64 / r64["iters"]) / 1e9, "rel_res": r64["rel_res"],
+        "kernel_ms": dict(zip(("spmv_dot", "update", "aypx"), k64)), "spmv_GBps": b_k1_64 / (1e-3 * k64[0]) / 1e9,
+        "layout": lay64,
     }
     irp = apcg.ir_plan_create(ctx, g["A"], None, apcg.ir_opts(rtol=1e-10, rtol_inner=1e-4, inner_check_every=10))
     msir, rir = timed(lambda: apcg.ir_plan_solve(irp, g["vb"], g["vx"]), max(1, args.steps // 3))
+    kir = apcg.ir_plan_profile(irp, g["vb"], g["vx"], 5)
+    layir = apcg.plan_layout(irp, "ir")
     apcg.call("apcg_ir_plan_destroy", V(irp))
     b_it32 = 8 * nnz + 4 * (n + 1) + 52 * n
+    b_k1_32 = 8 * nnz + 4 * (n + 1) + 8 * n
     out["mixed_ir"] = {
         "ms_per_solve": msir, "outer": rir["outer"], "inner_total": rir["inner_total"],
         "us_per_inner_iteration": 1e3 * msir / max(1, rir["inner_total"]),
         "GBps_per_inner_iteration": b_it32 / (1e-3 * msir / max(1, rir["inner_total"])) / 1e9, "rel_res": rir["rel_res"],
+        "kernel_ms": dict(zip(("residual64", "inner_spmv_dot", "inner_update", "inner_aypx"), kir)),
+        "inner_spmv_GBps": b_k1_32 / (1e-3 * kir[1]) / 1e9, "layout": layir,
     }
     out["speedup_ir_vs_fp64"] = ms64 / msir
     line = {"metric": "time to solution at rtol 1e-10 (float64 PCG vs float32-inner refinement)", "value": 1e3 / msir,
@@ -878,7 +888,7 @@ def bench_tfqmr(args):
     print(json.dumps(line), flush=True)
 
 
-NCU_CASES = ("c2", "c3", "c1p", "tfqmr", "stencil")
+NCU_CASES = ("c2", "c3", "c1p", "tfqmr", "stencil", "ir")
 
 
 def ncu_case(case="c2"):
@@ -887,7 +897,9 @@ def ncu_case(case="c2"):
     c3      the same on the 160^3 27-point variable-coefficient system (long-row K1, groups of 9);
     c1p     one whole-solve cluster launch on the 64^2 5-point system (persistent mode);
     tfqmr   set-up + 3 TFQMR iterations on the 128^3 7-point system (async mode);
-    stencil set-up + 3 CG iterations with the matrix-free 7-point operator on 128^3."""
+    stencil set-up + 3 CG iterations with the matrix-free 7-point operator on 128^3;
+    ir      the float32-inner refinement on the 160^3 27-point system: its float64 residual, then 3 inner
+            iterations with the float32 K1/K2/K3 launched one by one."""
     import ctypes as C
 
     import numpy as np
@@ -915,7 +927,7 @@ def ncu_case(case="c2"):
         apcg.call("apcg_cg_plan_destroy", V(plan))
         print(json.dumps({"ncu_case": case, "kernel_ms": ms}))
         return
-    p = single_problem({"c2": "c2", "c3": "c3", "c1p": "c1", "tfqmr": "c2"}[case], seed=0)
+    p = single_problem({"c2": "c2", "c3": "c3", "c1p": "c1", "tfqmr": "c2", "ir": "c3"}[case], seed=0)
     rowptr, col, val, b = t(p.A.rowptr), t(p.A.col), t(p.A.val), t(p.b)
     x = torch.zeros(p.n, dtype=torch.float64, device=dev)
     A = apcg.mat_wrap(rowptr, col, val)
@@ -925,6 +937,11 @@ def ncu_case(case="c2"):
         ms = apcg.cg_plan_profile(plan, vb, vx, 3)
         apcg.call("apcg_cg_plan_destroy", V(plan))
         print(json.dumps({"ncu_case": f"{case} setup + 3 iterations", "kernel_ms": ms}))
+    elif case == "ir":
+        plan = apcg.ir_plan_create(ctx, A, None, apcg.ir_opts(rtol=1e-10, inner_check_every=10))
+        ms = apcg.ir_plan_profile(plan, vb, vx, 3)
+        apcg.call("apcg_ir_plan_destroy", V(plan))
+        print(json.dumps({"ncu_case": "ir: residual + 3 inner iterations", "kernel_ms": ms}))
     elif case == "c1p":
         plan = apcg.cg_plan_create(ctx, A, apcg.cg_opts(rtol=RTOL, check_every=1, mode="persistent"))
         r = apcg.cg_plan_solve(plan, vb, vx)

@@ -519,6 +519,17 @@ APCG_API apcg_status apcg_ir_plan_solve(apcg_ir_plan plan, apcg_vec b, apcg_vec 
 APCG_API apcg_status apcg_ir_plan_destroy(apcg_ir_plan plan);
 /* The sliced-ELL copy the plan's SpMVs read (see apcg_cg_plan_layout; the float32 and float64 copies share it). */
 APCG_API apcg_status apcg_ir_plan_layout(apcg_ir_plan plan, apcg_plan_layout* out);
+/*
+ * Kernel timing for performance reports, as apcg_cg_plan_profile: one outer
+ * residual r = b - A x (float64, fused with the set-up of the inner solve),
+ * then `iters` float32 inner iterations with each of the three iteration
+ * kernels launched on its own between CUDA events, with no inner tolerance
+ * (keep iters well below the inner convergence count).  ms[0] = the residual
+ * kernel, ms[1..3] = the average durations of the inner SpMV + (p,Ap), the
+ * updates + Jacobi + (r,z),(r,r) and the search-direction update, in
+ * milliseconds.  x is read, not changed.  Blocks until the kernels are done.
+ */
+APCG_API apcg_status apcg_ir_plan_profile(apcg_ir_plan plan, apcg_vec b, apcg_vec x, int32_t iters, float* ms);
 APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
                                    const apcg_ir_opts* opts, apcg_ir_result* res);
 

@@ -235,6 +235,7 @@ PROTOS = {
     "apcg_ir_plan_solve": [P, P, P, C.POINTER(IrResult)],
     "apcg_ir_plan_destroy": [P],
     "apcg_ir_plan_layout": [P, C.POINTER(PlanLayout)],
+    "apcg_ir_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
     "apcg_expr_create": [P, i32, PP],
     "apcg_expr_destroy": [P],
@@ -652,6 +653,13 @@ def ir_opts(rtol=1e-10, atol=0.0, max_outer=50, max_inner=1000, rtol_inner=1e-4,
     o.rtol, o.atol, o.max_outer, o.max_inner = rtol, atol, max_outer, max_inner
     o.rtol_inner, o.inner_check_every = rtol_inner, inner_check_every
     return o
+
+
+def ir_plan_profile(plan, b, x, iters: int) -> list[float]:
+    """[residual, inner K1, inner K2, inner K3] kernel times in ms (see apcg_ir_plan_profile)."""
+    ms = (C.c_float * 4)()
+    call("apcg_ir_plan_profile", C.c_void_p(plan), C.c_void_p(b), C.c_void_p(x), iters, ms)
+    return [float(v) for v in ms]
 
 
 def ir_plan_create(ctx, A64, A32, opts: IrOpts):

@@ -73,7 +73,10 @@ void ir_destroy(apcg_ir_plan P) {
   delete P;
 }
 
-apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cudaStream_t s) {
+// The outer residual and the set-up of the inner solve (its tolerance rtol_inner ||r32||, at most max_inner
+// iterations).
+apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cudaStream_t s, double rtol_inner,
+                            int32_t max_inner) {
   ir::ResidualArgs a;
   a.n = P->n;
   a.b = b;
@@ -86,8 +89,8 @@ apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cu
   a.opartials = P->opartials;
   a.ist = P->core.st;
   a.ipartials = P->core.partials;
-  a.rtol_inner = P->opts.rtol_inner;
-  a.max_inner = P->core.max_it;
+  a.rtol_inner = rtol_inner;
+  a.max_inner = max_inner;
   a.inner_k = P->core.k;
   if (P->S.n > 0) {
     const int g = P->grid_res;
@@ -369,7 +372,7 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
   int64_t launches = 0;
   apcg_status st = APCG_OK;
   for (int32_t k = 0;; ++k) {
-    st = launch_residual(P, bp, xp, s);
+    st = launch_residual(P, bp, xp, s, P->opts.rtol_inner, P->core.max_it);
     if (st != APCG_OK) break;
     launches += 1;
     cudaError_t e = cudaMemcpyAsync(ho, P->ost, sizeof(IrState), cudaMemcpyDeviceToHost, s);
@@ -429,6 +432,51 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
   count_kernels(launches);
   apcg_status st2 = op.finish();
   return st != APCG_OK ? st : st2;
+}
+
+apcg_status apcg_ir_plan_profile(apcg_ir_plan P, apcg_vec b, apcg_vec x, int32_t iters, float* ms) {
+  APCG_CHECK(P && b && x, "NULL argument");
+  APCG_CHECK(b->dtype == APCG_F64 && x->dtype == APCG_F64, "b and x must be float64");
+  APCG_CHECK(b->n == P->n && x->n == P->n, "b/x length differs from the matrix size %d", P->n);
+  APCG_CHECK(iters >= 1 && ms, "iters must be >= 1 and ms non-NULL");
+  APCG_CHECK(P->n > 0, "empty system");
+  cudaStream_t s = P->ctx->stream;
+  OpScope op(P->ctx);
+  op.read(P->id_a64).read(P->id_a32).read(b->id).read(x->id).rw(P->id);
+  APCG_TRY(op.begin());
+  cudaEvent_t ev[5];
+  for (auto& e : ev) APCG_CUDA(cudaEventCreate(&e));
+  float tot[4] = {0.f, 0.f, 0.f, 0.f};
+  // no inner tolerance and no cap: every inner iteration runs
+  cudaEventRecord(ev[0], s);
+  apcg_status st = launch_residual(P, static_cast<const double*>(b->dptr), static_cast<const double*>(x->dptr), s,
+                                   0.0, 1 << 30);
+  cudaEventRecord(ev[1], s);
+  cudaEventSynchronize(ev[1]);
+  cudaEventElapsedTime(&tot[0], ev[0], ev[1]);
+  CgCore<float> c = P->core;
+  c.max_it = 1 << 30;
+  for (int32_t i = 0; i < iters && st == APCG_OK; ++i) {
+    cudaEventRecord(ev[1], s);
+    st = core_k1(c, P->d32, s, false);
+    cudaEventRecord(ev[2], s);
+    if (st == APCG_OK) st = core_k2(c, P->d32, s, false, 0.0, 0, 0);
+    cudaEventRecord(ev[3], s);
+    if (st == APCG_OK) st = core_k3(c, P->d32, s, false, 0.0);
+    cudaEventRecord(ev[4], s);
+    cudaEventSynchronize(ev[4]);
+    for (int k = 1; k < 4; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      tot[k] += t;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  count_kernels(1 + 3 * (int64_t)iters);
+  APCG_TRY(st);
+  ms[0] = tot[0];
+  for (int k = 1; k < 4; ++k) ms[k] = tot[k] / iters;
+  return op.finish();
 }
 
 apcg_status apcg_ir_plan_layout(apcg_ir_plan P, apcg_plan_layout* out) {

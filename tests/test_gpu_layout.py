@@ -215,3 +215,22 @@ def test_ir_layout_and_accuracy(ctx, name):
     assert true_rel <= 1.05e-10 and abs(true_rel - res["rel_res"]) <= 1e-12
     assert _rel(x, ref["x"]) <= 1e-6
     s.close()
+
+
+def test_ir_profile_times_kernels_and_leaves_x(ctx):
+    A, _ = _case("diff27_13")
+    b = rhs_from_solution(A, np.random.default_rng(6).uniform(-1, 1, A.n))
+    s = _Sys(A, b)
+    x0 = np.random.default_rng(7).uniform(-1, 1, A.n)
+    s.keep[4].copy_(torch.from_numpy(x0))
+    plan = apcg.ir_plan_create(ctx, s.M, None, apcg.ir_opts(rtol=1e-10))
+    apcg.reset_counters()
+    ms = apcg.ir_plan_profile(plan, s.vb, s.vx, 4)
+    launches = apcg.get_counters()["kernel_launches"]
+    with pytest.raises(apcg.ApcgError):
+        apcg.ir_plan_profile(plan, s.vb, s.vx, 0)
+    apcg.call("apcg_ir_plan_destroy", V(plan))
+    assert len(ms) == 4 and all(t > 0 for t in ms), ms
+    assert launches == 1 + 3 * 4
+    assert np.array_equal(s.x, x0)
+    s.close()
