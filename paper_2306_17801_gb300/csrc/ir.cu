@@ -481,9 +481,11 @@ apcg_status apcg_ir_plan_profile(apcg_ir_plan P, apcg_vec b, apcg_vec x, int32_t
 
 apcg_status apcg_ir_plan_layout(apcg_ir_plan P, apcg_plan_layout* out) {
   APCG_CHECK(P && out, "plan or out is NULL");
-  // the float32 SpMV's group: 8 where the rows are long, else one entry at a time
-  describe_layout(P->A32.sptr != nullptr, dev::col_format(P->A32), P->A32.long_rows ? 8 : 0, P->A32.nslices,
-                  P->padded, out);
+  // the float32 SpMV's group (the K1 instance choice): 9 for 27-entry rows with per-slice offset lists, else
+  // 8 where the rows are long, else one entry at a time
+  const int32_t lr = P->A32.long_rows;
+  const int32_t group = lr == 0 ? 0 : (P->A32.poff && lr == 9) ? 9 : 8;
+  describe_layout(P->A32.sptr != nullptr, dev::col_format(P->A32), group, P->A32.nslices, P->padded, out);
   return APCG_OK;
 }
 

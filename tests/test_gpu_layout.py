@@ -206,6 +206,8 @@ def test_ir_layout_and_accuracy(ctx, name):
     try:
         lay = apcg.plan_layout(plan, "ir")
         assert lay["col_format"] == ("index" if fmt == "offset16" else fmt), lay  # no 16-bit offsets here
+        if name == "diff27_13":  # 27-entry rows: whole groups of 9 with the offset lists
+            assert lay["group"] == 9, lay
         res = apcg.ir_plan_solve(plan, s.vb, s.vx)
     finally:
         apcg.call("apcg_ir_plan_destroy", V(plan))
