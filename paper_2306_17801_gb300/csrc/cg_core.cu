@@ -163,16 +163,27 @@ __device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma) {
   }
 }
 
-// K1 (G: group size of the long-row path; CF: column format, dev::ColFormat)
-template <bool HOST, bool LONG, class T, int G = 8, int CF = dev::kColIndex>
+// K1 (G: group size of the long-row path; CF: column format, dev::ColFormat; STAGED: float32 values staged
+// in shared memory by bulk copies, dev::sell_spmv_staged, with stage_smem_bytes of dynamic shared memory)
+template <bool HOST, bool LONG, class T, int G = 8, int CF = dev::kColIndex, bool STAGED = false>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   if (!HOST && read_done(a.st)) return;
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
-  dev::sell_spmv<true, LONG, T, G, CF>(a.A, a.p, [&](int32_t i, T s, T p_i) {
-                                     a.w[i] = s;
-                                     v[0] = fma(p_i, s, v[0]);
-                                   });
+  auto epi = [&](int32_t i, T s, T p_i) {
+    a.w[i] = s;
+    v[0] = fma(p_i, s, v[0]);
+  };
+  if constexpr (STAGED) {
+    static_assert(std::is_same<T, float>::value && CF == dev::kColPattern && LONG, "staged K1: float32 offset lists");
+    extern __shared__ __align__(128) unsigned char stage_smem[];
+    const int w = threadIdx.x >> 5;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_smem) + 2 * w;
+    float* stage = reinterpret_cast<float*>(stage_smem + dev::kStageBarrierBytes) + (size_t)w * 2 * a.A.stage_cap * 32;
+    dev::sell_spmv_staged<true, G>(a.A, a.p, stage, bars, &a.st->done, kDoneBreakdown, epi);
+  } else {
+    dev::sell_spmv<true, LONG, T, G, CF>(a.A, a.p, epi);
+  }
   T tot[1];
   if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0]);
 }
@@ -356,9 +367,10 @@ __global__ void __launch_bounds__(kThreads, 4) k3_kernel(Args<T> a, double beta_
 }
 
 template <class K>
-int occupancy_grid(K kernel, int sms, int64_t want) {
+int occupancy_grid(K kernel, int sms, int64_t want, size_t dyn_smem = 0) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, dyn_smem) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -398,9 +410,22 @@ void* k1_instance_d(const CgCore<T>& c) {
   }
   // float32 with per-slice offset lists: 27-entry rows in three whole groups of 9 (no column loads, so the
   // larger group costs no occupancy; 160^3 refinement 86.2 -> 81.6 ms)
-  if constexpr (CF == dev::kColPattern && std::is_same<T, float>::value)
+  if constexpr (CF == dev::kColPattern && std::is_same<T, float>::value) {
+    if (c.A.long_rows && c.A.stage_cap > 0)
+      return c.A.long_rows == 9 ? (void*)k1_kernel<HOST, true, T, 9, CF, true>
+                                : (void*)k1_kernel<HOST, true, T, 8, CF, true>;
     if (c.A.long_rows == 9) return (void*)k1_kernel<HOST, true, T, 9, CF>;
+  }
   return c.A.long_rows ? (void*)k1_kernel<HOST, true, T, 8, CF> : (void*)k1_kernel<HOST, false, T, 8, CF>;
+}
+
+// Dynamic shared memory of the plan's K1 instance (the staged float32 form only).
+template <class T>
+int k1_dyn_smem(const CgCore<T>& c) {
+  if constexpr (std::is_same<T, float>::value)
+    if (c.S.n == 0 && c.A.poff && c.A.long_rows && c.A.stage_cap > 0)
+      return dev::stage_smem_bytes(c.A.stage_cap, kThreads / 32);
+  return 0;
 }
 
 template <bool HOST, class T>
@@ -414,7 +439,8 @@ template <bool HOST, class T>
 apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
   if (c.S.n > 0) return k1_stencil_dispatch<HOST>(c, a, s);
   void* args[] = {const_cast<Args<T>*>(&a)};
-  APCG_CUDA(cudaLaunchKernel(k1_instance<HOST>(c), dim3(c.grid_spmv), dim3(kThreads), args, 0, s));
+  APCG_CUDA(cudaLaunchKernel(k1_instance<HOST>(c), dim3(c.grid_spmv), dim3(kThreads), args, (size_t)k1_dyn_smem(c),
+                             s));
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
 }
@@ -429,8 +455,15 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
   const int64_t vec_blocks = (((int64_t)c.n / V16<T>::E) + (int64_t)kThreads * kUpdV - 1) / ((int64_t)kThreads * kUpdV);
   if (c.S.n > 0)
     c.grid_spmv = occupancy_grid((void*)k1_stencil_kernel<false, 7, T>, sms, ((int64_t)c.n + kThreads - 1) / kThreads);
-  else
-    c.grid_spmv = occupancy_grid(k1_instance<false>(c), sms, spmv_blocks);
+  else {
+    const int dyn = k1_dyn_smem(c);
+    if (dyn > 48 * 1024) {  // above the default limit: opt in (both instances, once per plan)
+      cudaFuncSetAttribute(k1_instance<false>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+      cudaFuncSetAttribute(k1_instance<true>(c), cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+      cudaGetLastError();
+    }
+    c.grid_spmv = occupancy_grid(k1_instance<false>(c), sms, spmv_blocks, (size_t)dyn);
+  }
   c.grid_vec = occupancy_grid((void*)k2_kernel<false, T>, sms, vec_blocks);
 }
 

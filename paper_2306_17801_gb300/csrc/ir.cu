@@ -252,6 +252,8 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
     P->A64.val = sval64;
   }
   P->A32.long_rows = P->A64.long_rows = L.long_rows;
+  // float32 offset-list SpMV of long rows: stage each warp's next slice of values in shared memory
+  P->A32.stage_cap = (L.pattern && L.long_rows) ? std::min(L.max_width, dev::kStageMaxWidth) : 0;
   P->padded = L.padded;
   c.A = P->A32;
   core_configure(c, S.nnz, sms);  // the SpMV kernel instance depends on the row length

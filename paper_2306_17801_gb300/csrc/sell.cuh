@@ -49,6 +49,8 @@ struct SellView {
   const int32_t* __restrict__ poff = nullptr;  // [sptr[nslices] / 32] per-slice column offsets (kColPattern)
   const TV* __restrict__ val = nullptr;        // [sptr[nslices]]
   int32_t long_rows = 0;  // 0: one entry at a time; else the group size G of the grouped path (8 or 9)
+  int32_t stage_cap = 0;  // float32 offset-list SpMV: slices of at most this many entries per row are staged
+                          // in shared memory (0: none)
 };
 
 template <class TV>
@@ -187,6 +189,158 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
       }
     }
     if (row < A.n) epi(row, acc, x_own);
+  }
+}
+
+// ---------------------------------------------------------------- staged float32 SpMV
+//
+// The float32 SpMV over per-slice offset lists streams 4 bytes per entry and
+// is bound by how many bytes each SM keeps in flight: with the values held in
+// registers, 48 registers per thread leave five blocks per SM, each warp with
+// one group of loads outstanding.  The staged form moves each warp's next
+// slice of values into shared memory with one bulk copy (the TMA engine,
+// cp.async.bulk, completion counted on an mbarrier) while the warp works on
+// the current slice, so a whole slice per warp is in flight without using
+// registers.  Every wait on an mbarrier is bounded.
+
+constexpr int kStageMaxWidth = 27;                // entries per row of the widest staged slice
+constexpr uint32_t kStageSpinLimit = 1u << 22;    // try_wait polls before a wait gives up
+constexpr int kStageBarrierBytes = 128;           // mbarriers at the front of the dynamic shared memory
+
+// Dynamic shared memory of the staged K1: two slice buffers and two mbarriers per warp.
+__host__ __device__ constexpr int stage_smem_bytes(int cap, int warps) {
+  return kStageBarrierBytes + warps * 2 * cap * 32 * (int)sizeof(float);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bulk copy of bytes (a multiple of 16; both addresses 16-byte aligned) from global to shared memory,
+// completing a transaction of that many bytes on bar (one arrival by the calling thread).
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Waits until bar completes the phase of the given parity; false after kStageSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kStageSpinLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// sell_spmv for float32 values and kColPattern with the values staged as above.  stage holds this warp's two
+// buffers of A.stage_cap * 32 floats, bars its two mbarriers.  Slices wider than A.stage_cap read their
+// values from global memory.  A wait that gives up sets *fail to fail_code, lets the warp's copies in flight
+// land (bounded again) and ends the warp's sweep.  All 32 lanes must call this function together.
+template <bool OWN_X, int G, class Epi>
+__device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const float* __restrict__ x, float* stage,
+                                                 uint64_t* bars, int32_t* fail, int32_t fail_code, Epi epi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int32_t cap_entries = A.stage_cap * 32;
+  const int32_t last = A.n - 1;
+  if (lane == 0) {
+    mbar_init(&bars[0]);
+    mbar_init(&bars[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // slice offsets of the current, the next and the one after (loaded a sweep step ahead)
+  int32_t b_cur = 0, e_cur = 0, b_nx = 0, e_nx = 0, b_far = 0, e_far = 0;
+  if (gwarp < A.nslices) {
+    b_cur = __ldg(A.sptr + gwarp);
+    e_cur = __ldg(A.sptr + gwarp + 1);
+  }
+  if (gwarp + nwarps < A.nslices) {
+    b_nx = __ldg(A.sptr + gwarp + nwarps);
+    e_nx = __ldg(A.sptr + gwarp + nwarps + 1);
+  }
+  uint32_t parity = 0u;   // bit b: parity of buffer b's next phase
+  uint32_t pending = 0u;  // bit b: a copy into buffer b has been issued and not waited for
+  int buf = 0;            // buffer of the current slice
+  bool cur_staged = gwarp < A.nslices && e_cur > b_cur && e_cur - b_cur <= cap_entries;
+  if (cur_staged) {
+    if (lane == 0) bulk_to_smem(stage, A.val + b_cur, (uint32_t)(e_cur - b_cur) * 4u, &bars[0]);
+    pending |= 1u;
+  }
+  bool failed = false;
+  for (int64_t s = gwarp; s < A.nslices; s += nwarps) {
+    // the next slice's values into the other buffer (its previous contents were consumed before the
+    // __syncwarp that ended the last step)
+    const bool has_next = s + nwarps < A.nslices;
+    const bool nx_staged = has_next && e_nx > b_nx && e_nx - b_nx <= cap_entries;
+    if (nx_staged) {
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_to_smem(stage + (buf ^ 1) * cap_entries, A.val + b_nx, (uint32_t)(e_nx - b_nx) * 4u, &bars[buf ^ 1]);
+      }
+      pending |= 1u << (buf ^ 1);
+    }
+    if (s + 2 * nwarps < A.nslices) {
+      b_far = __ldg(A.sptr + s + 2 * nwarps);
+      e_far = __ldg(A.sptr + s + 2 * nwarps + 1);
+    }
+    const int32_t row = (int32_t)(s * 32 + lane);
+    float x_own = 0.f;
+    if (OWN_X && row < A.n) x_own = ld_ro(x + row);
+    const int32_t* op = A.poff + (b_cur >> 5);
+    const int32_t width = (e_cur - b_cur) >> 5;
+    const float* sv;
+    if (cur_staged) {
+      const bool ok = mbar_wait(&bars[buf], (parity >> buf) & 1u);
+      if (!__all_sync(kFull, ok)) {  // the copy stays pending, with its phase's parity
+        failed = true;
+        break;
+      }
+      parity ^= 1u << buf;
+      pending &= ~(1u << buf);
+      sv = stage + buf * cap_entries + lane;
+    } else {
+      sv = A.val + b_cur + lane;
+    }
+    float acc = 0.f;
+    int32_t k = 0;
+    for (; k + G <= width; k += G) {
+      int32_t j[G];
+      float xv[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) j[g] = min(max(row + __ldg(op + k + g), 0), last);
+#pragma unroll
+      for (int g = 0; g < G; ++g) xv[g] = ld_ro(x + j[g]);
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc = fmaf(sv[32 * (k + g)], xv[g], acc);
+    }
+    for (; k < width; ++k) acc = fmaf(sv[32 * k], ld_ro(x + min(max(row + __ldg(op + k), 0), last)), acc);
+    if (row < A.n) epi(row, acc, x_own);
+    __syncwarp();
+    buf ^= 1;
+    b_cur = b_nx;
+    e_cur = e_nx;
+    b_nx = b_far;
+    e_nx = e_far;
+    cur_staged = nx_staged;
+  }
+  if (failed) {
+    if (lane == 0) atomicMax(fail, fail_code);
+    // let the copies still in flight land before the shared memory goes away
+    for (int b = 0; b < 2; ++b)
+      if (pending & (1u << b)) (void)mbar_wait(&bars[b], (parity >> b) & 1u);
   }
 }
 
