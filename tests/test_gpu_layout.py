@@ -86,12 +86,15 @@ def _case(name):
         j = rng.integers(0, A.n, i.size)
         keep = np.abs(i - j) > 60
         return _add_couplings(A, zip(i[keep], j[keep]), 0.25), "offset16"
+    if name == "mixed_width":  # 27-point rows plus couplings 1000 rows away: slices of 18..29 entries per row
+        A = single_problem("c3", size=13).A
+        return _add_couplings(A, [(i, i + 1000) for i in range(A.n // 2)], 0.1), "pattern"
     if name == "far":  # random SPD with entries beyond 32767 of the diagonal
         return random_spd_csr(40_000, 2e-4, rng, dominance=0.2), "index"
     raise ValueError(name)
 
 
-CASES = ["lap5_48", "lap7_21", "diff27_13", "one_row", "unsorted", "scattered", "far"]
+CASES = ["lap5_48", "lap7_21", "diff27_13", "one_row", "unsorted", "scattered", "mixed_width", "far"]
 
 
 class _Sys:
@@ -193,11 +196,13 @@ def test_tfqmr_layout_and_solution(ctx, name):
     s.close()
 
 
-@pytest.mark.parametrize("name", ["lap7_21", "diff27_13", "unsorted", "far"])
+@pytest.mark.parametrize("name", ["lap7_21", "diff27_13", "mixed_width", "unsorted", "far"])
 def test_ir_layout_and_accuracy(ctx, name):
     """Float32 inner PCG (rtol 1e-4) inside float64 refinement to rtol 1e-10: the GPU's true residual meets
     the tolerance and x agrees with the oracle's float64 CG solution to 1e-12 within 1e-6 (the bar of the
-    refinement's full-size test; both lie within the conditioning bound of the same solution)."""
+    refinement's full-size test; both lie within the conditioning bound of the same solution).  diff27_13
+    and mixed_width run the shared-memory staged float32 SpMV; mixed_width's slices wider than 27 entries
+    per row read their values from global memory instead."""
     A, fmt = _case(name)
     b = rhs_from_solution(A, np.random.default_rng(4).uniform(-1, 1, A.n))
     ref = oracle.pcg(A, b, rtol=1e-12, check_every=1)
