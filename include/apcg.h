@@ -530,6 +530,18 @@ APCG_API apcg_status apcg_ir_plan_layout(apcg_ir_plan plan, apcg_plan_layout* ou
  * milliseconds.  x is read, not changed.  Blocks until the kernels are done.
  */
 APCG_API apcg_status apcg_ir_plan_profile(apcg_ir_plan plan, apcg_vec b, apcg_vec x, int32_t iters, float* ms);
+/*
+ * Test hook for the bounded waits of the staged float32 SpMV (the inner SpMV
+ * of a plan whose matrix takes per-slice offset lists with long rows: each
+ * warp bulk-copies its next slice of values into shared memory and waits on
+ * an mbarrier, about 0.16 s at most).  With on != 0 every copy announces 16 bytes
+ * more than it moves, so every such wait runs out: the SpMV gives up, the
+ * solve reports APCG_ERR_TIMEOUT (res->reason = APCG_BREAKDOWN) and the
+ * context stays usable.  on = 0 restores normal operation.  Nothing faults:
+ * the copies themselves are unchanged.  Returns APCG_ERR_UNSUPPORTED for a
+ * plan without a staged SpMV.  Blocks until the plan's graph is re-captured.
+ */
+APCG_API apcg_status apcg_ir_plan_test_stall_copies(apcg_ir_plan plan, int32_t on);
 APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
                                    const apcg_ir_opts* opts, apcg_ir_result* res);
 

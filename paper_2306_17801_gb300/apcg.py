@@ -28,6 +28,7 @@ ERR = {
     -7: "APCG_ERR_NOT_READY",
     -8: "APCG_ERR_BREAKDOWN",
 }
+ERR_TIMEOUT, ERR_UNSUPPORTED = -5, -6
 STREAM_DEFAULT_BLOCKING, STREAM_GLOBAL_BLOCKING = 0, 1
 READ, WRITE, READ_WRITE = 1, 2, 3
 JOIN_DESTROY, JOIN_SYNC, JOIN_NO_SYNC = 0, 1, 2
@@ -236,6 +237,7 @@ PROTOS = {
     "apcg_ir_plan_destroy": [P],
     "apcg_ir_plan_layout": [P, C.POINTER(PlanLayout)],
     "apcg_ir_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
+    "apcg_ir_plan_test_stall_copies": [P, i32],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
     "apcg_expr_create": [P, i32, PP],
     "apcg_expr_destroy": [P],

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
     const int w = threadIdx.x >> 5;
     uint64_t* bars = reinterpret_cast<uint64_t*>(stage_smem) + 2 * w;
     float* stage = reinterpret_cast<float*>(stage_smem + dev::kStageBarrierBytes) + (size_t)w * 2 * a.A.stage_cap * 32;
-    dev::sell_spmv_staged<true, G>(a.A, a.p, stage, bars, &a.st->done, kDoneBreakdown, epi);
+    dev::sell_spmv_staged<true, G>(a.A, a.p, stage, bars, &a.st->done, kDoneTimeout, epi);
   } else {
     dev::sell_spmv<true, LONG, T, G, CF>(a.A, a.p, epi);
   }

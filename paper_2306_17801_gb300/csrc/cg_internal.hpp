@@ -12,7 +12,14 @@
 namespace apcg {
 
 // 'done' word of the device state block.
-enum : int32_t { kDoneRunning = 0, kDoneConverged = 1, kDoneNotConverged = 2, kDoneBreakdown = 3, kDoneBadDiagonal = 4 };
+enum : int32_t {
+  kDoneRunning = 0,
+  kDoneConverged = 1,
+  kDoneNotConverged = 2,
+  kDoneBreakdown = 3,
+  kDoneBadDiagonal = 4,
+  kDoneTimeout = 5  // a bounded device wait ran out (the staged float32 SpMV)
+};
 
 // Device-resident scalars of one solve (the managed scalars of Sec. 3.2).
 struct CgState {

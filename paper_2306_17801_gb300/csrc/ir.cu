@@ -429,6 +429,11 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
     res->inner_total += hi->iter;
     launches += (int64_t)hi->body_runs * 3 * P->core.k;
     res->outer = k + 1;
+    if (hi->done == kDoneTimeout) {  // a bounded wait in the staged SpMV ran out: the correction is not usable
+      res->reason = APCG_BREAKDOWN;
+      st = set_error(APCG_ERR_TIMEOUT, "a bounded device wait ran out (staged float32 SpMV)");
+      break;
+    }
   }
   res->kernel_launches = launches;
   count_kernels(launches);
@@ -476,9 +481,25 @@ apcg_status apcg_ir_plan_profile(apcg_ir_plan P, apcg_vec b, apcg_vec x, int32_t
   for (auto& e : ev) cudaEventDestroy(e);
   count_kernels(1 + 3 * (int64_t)iters);
   APCG_TRY(st);
+  CgState hs;
+  APCG_CUDA(cudaMemcpy(&hs, P->core.st, sizeof(hs), cudaMemcpyDeviceToHost));
+  if (hs.done == kDoneTimeout) return set_error(APCG_ERR_TIMEOUT, "a bounded device wait ran out (staged float32 SpMV)");
   ms[0] = tot[0];
   for (int k = 1; k < 4; ++k) ms[k] = tot[k] / iters;
   return op.finish();
+}
+
+apcg_status apcg_ir_plan_test_stall_copies(apcg_ir_plan P, int32_t on) {
+  APCG_CHECK(P, "plan is NULL");
+  if (P->A32.stage_cap == 0 || P->S.n > 0)
+    return set_error(APCG_ERR_UNSUPPORTED, "the plan's float32 SpMV stages no values");
+  P->A32.stage_tx_extra = on ? 16u : 0u;
+  P->core.A.stage_tx_extra = P->A32.stage_tx_extra;
+  // the captured graph holds the kernels' arguments by value: capture it again
+  core_release_graph(P->core);
+  APCG_TRY(core_build_graph(P->core, P->d32, P->ctx->stream));
+  APCG_CUDA(cudaStreamSynchronize(P->ctx->stream));
+  return APCG_OK;
 }
 
 apcg_status apcg_ir_plan_layout(apcg_ir_plan P, apcg_plan_layout* out) {

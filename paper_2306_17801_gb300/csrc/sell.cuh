@@ -51,6 +51,8 @@ struct SellView {
   int32_t long_rows = 0;  // 0: one entry at a time; else the group size G of the grouped path (8 or 9)
   int32_t stage_cap = 0;  // float32 offset-list SpMV: slices of at most this many entries per row are staged
                           // in shared memory (0: none)
+  uint32_t stage_tx_extra = 0;  // test hook: bytes each staged copy is expected to move beyond what it moves
+                                // (nonzero makes every wait on the copies run out; 0 in normal use)
 };
 
 template <class TV>
@@ -204,7 +206,7 @@ __device__ __forceinline__ void sell_spmv(const SellView<TV>& A, const T* __rest
 // registers.  Every wait on an mbarrier is bounded.
 
 constexpr int kStageMaxWidth = 27;                // entries per row of the widest staged slice
-constexpr uint32_t kStageSpinLimit = 1u << 22;    // try_wait polls before a wait gives up
+constexpr uint32_t kStageSpinLimit = 1u << 16;    // try_wait polls before a wait gives up (about 0.16 s)
 constexpr int kStageBarrierBytes = 128;           // mbarriers at the front of the dynamic shared memory
 
 // Dynamic shared memory of the staged K1: two slice buffers and two mbarriers per warp.
@@ -219,9 +221,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
 }
 
 // Bulk copy of bytes (a multiple of 16; both addresses 16-byte aligned) from global to shared memory,
-// completing a transaction of that many bytes on bar (one arrival by the calling thread).
-__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+// completing a transaction of that many bytes on bar (one arrival by the calling thread, which announces
+// bytes + extra: extra is 0 except under the test hook SellView::stage_tx_extra).
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint32_t extra) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes + extra)
                : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
@@ -229,17 +233,23 @@ __device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_
                : "memory");
 }
 
-// Waits until bar completes the phase of the given parity; false after kStageSpinLimit polls.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok)
+               : "r"(bar), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+
+// Waits until bar completes the phase of the given parity; false after kStageSpinLimit polls.  A poll
+// that finds the phase still open suspends the thread for a time the hardware chooses (about 2.5 us on
+// GB300), so a wait that runs out takes about 0.16 s.  Bounding the wait by a clock read instead made the
+// staged SpMV 45 us per launch slower (the compiler then scheduled the whole loop differently).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kStageSpinLimit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < kStageSpinLimit; ++i)
+    if (mbar_try_wait(a, parity)) return true;
   return false;
 }
 
@@ -276,7 +286,7 @@ __device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const
   int buf = 0;            // buffer of the current slice
   bool cur_staged = gwarp < A.nslices && e_cur > b_cur && e_cur - b_cur <= cap_entries;
   if (cur_staged) {
-    if (lane == 0) bulk_to_smem(stage, A.val + b_cur, (uint32_t)(e_cur - b_cur) * 4u, &bars[0]);
+    if (lane == 0) bulk_to_smem(stage, A.val + b_cur, (uint32_t)(e_cur - b_cur) * 4u, &bars[0], A.stage_tx_extra);
     pending |= 1u;
   }
   bool failed = false;
@@ -288,7 +298,8 @@ __device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const
     if (nx_staged) {
       if (lane == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_to_smem(stage + (buf ^ 1) * cap_entries, A.val + b_nx, (uint32_t)(e_nx - b_nx) * 4u, &bars[buf ^ 1]);
+        bulk_to_smem(stage + (buf ^ 1) * cap_entries, A.val + b_nx, (uint32_t)(e_nx - b_nx) * 4u, &bars[buf ^ 1],
+                     A.stage_tx_extra);
       }
       pending |= 1u << (buf ^ 1);
     }

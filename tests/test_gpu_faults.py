@@ -4,8 +4,10 @@ A NaN or infinity in the right-hand side or the start vector must end every
 solver and mode with a reported breakdown (not a hang, not a CUDA error), a
 NaN system inside a batch must fail alone, bad arguments must be rejected
 before anything is enqueued, and the context must stay usable for the next
-solve.  The library has no device-side spin-waits, so no kernel can wait on a
-flag that is never set.
+solve.  The only device-side waits are those of the refinement's staged
+float32 SpMV on its bulk copies (mbarriers), each bounded by polls and time; a
+test hook makes every one of them run out, without any fault, and the solve
+must report the timeout.
 """
 
 import ctypes as C
@@ -189,3 +191,49 @@ def test_malformed_csr_is_rejected_at_plan_creation(ctx, kind, solver, mode):
             apcg.call(f, V(h))
     ok, _ = _cg(ctx, *_system(12), solver="cg" if solver == "ir" else solver, mode=mode or "async_graph", rtol=1e-8)
     assert ok["reason"] == "converged"
+
+
+def test_staged_spmv_wait_runs_out_and_reports_timeout(ctx):
+    """The refinement's staged float32 SpMV waits on mbarriers for its bulk copies, each wait bounded (2^16
+    polls, about 0.16 s).
+    The test hook makes every copy announce 16 bytes more than it moves, so every wait runs out (nothing
+    faults: the copies are unchanged): the solve must return APCG_ERR_TIMEOUT, and the same plan, with the
+    hook off, and the context must solve normally afterwards."""
+    from synthetic import single_problem
+
+    A = single_problem("c3", size=13).A  # 27-entry rows with per-slice offset lists: the staged SpMV
+    b = rhs_from_solution(A, np.random.default_rng(8).uniform(-1, 1, A.n))
+    keep = [_t(A.rowptr), _t(A.col), _t(A.val), _t(b), torch.zeros(A.n, dtype=torch.float64, device="cuda:0")]
+    M = apcg.mat_wrap(keep[0], keep[1], keep[2])
+    vb, vx = apcg.vec_wrap(keep[3]), apcg.vec_wrap(keep[4])
+    plan = apcg.ir_plan_create(ctx, M, None, apcg.ir_opts(rtol=1e-10))
+    try:
+        assert apcg.plan_layout(plan, "ir")["col_format"] == "pattern"
+        apcg.call("apcg_ir_plan_test_stall_copies", V(plan), 1)
+        with pytest.raises(apcg.ApcgError) as ei:
+            apcg.ir_plan_solve(plan, vb, vx)
+        assert ei.value.status == apcg.ERR_TIMEOUT and "bounded device wait" in str(ei.value)
+        apcg.call("apcg_ir_plan_test_stall_copies", V(plan), 0)
+        keep[4].zero_()
+        res = apcg.ir_plan_solve(plan, vb, vx)
+        assert res["reason"] == "converged" and res["rel_res"] <= 1.05e-10, res
+    finally:
+        apcg.call("apcg_ir_plan_destroy", V(plan))
+        for h, f in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (M, "apcg_mat_destroy")):
+            apcg.call(f, V(h))
+    ok, _ = _cg(ctx, *_system(12), rtol=1e-8)
+    assert ok["reason"] == "converged"
+
+
+def test_stall_hook_needs_a_staged_plan(ctx):
+    A, b = _system(12)  # 5-point rows: no staged SpMV
+    keep = [_t(A.rowptr), _t(A.col), _t(A.val)]
+    M = apcg.mat_wrap(*keep)
+    plan = apcg.ir_plan_create(ctx, M, None, apcg.ir_opts(rtol=1e-10))
+    try:
+        with pytest.raises(apcg.ApcgError) as ei:
+            apcg.call("apcg_ir_plan_test_stall_copies", V(plan), 1)
+        assert ei.value.status == apcg.ERR_UNSUPPORTED
+    finally:
+        apcg.call("apcg_ir_plan_destroy", V(plan))
+        apcg.call("apcg_mat_destroy", V(M))
