@@ -11,6 +11,7 @@ from .oracle import (  # noqa: F401
     load,
     dot,
     spmv,
+    spmv_f32,
     diagonal,
     pcg,
     tfqmr,

@@ -84,7 +84,7 @@ def load():
             lib.oracle_diagonal.restype = C.c_int
             lib.oracle_pcg.argtypes = [i64, P, P, P, P, P, f64, f64, i32, i32, i32, P, P, P, P, P, i32, C.POINTER(_Res)]
             lib.oracle_pcg.restype = C.c_int
-            lib.oracle_pcg_f32.argtypes = [i64, P, P, P, P, P, f32, i32, i32, C.POINTER(_Res)]
+            lib.oracle_pcg_f32.argtypes = [i64, P, P, P, P, P, f32, i32, i32, i32, P, P, P, i32, C.POINTER(_Res)]
             lib.oracle_pcg_f32.restype = C.c_int
             lib.oracle_ir.argtypes = [i64, P, P, P, P, P, P, f64, i32, f32, i32, i32, C.POINTER(_IrRes)]
             lib.oracle_ir.restype = C.c_int
@@ -126,9 +126,10 @@ def spmv(A, x) -> np.ndarray:
     return y
 
 
-def spmv_f32(A, x) -> np.ndarray:
+def spmv_f32(A, x, val32=None) -> np.ndarray:
+    """y = A x in float32 (A's values rounded to float32, or val32), float32 accumulation in column order."""
     rowptr, col, _ = _csr(A)
-    val = np.ascontiguousarray(A.val, dtype=np.float32)
+    val = np.ascontiguousarray(A.val if val32 is None else val32, dtype=np.float32)
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.empty(A.n, dtype=np.float32)
     load().oracle_spmv_f32(A.n, _p(rowptr), _p(col), _p(val), _p(x), _p(y))
@@ -198,15 +199,24 @@ def stencil_apply(dims, offsets, weights, x, mutation=0) -> np.ndarray:
     return y
 
 
-def pcg_f32(A, bf, rtol=1e-4, max_it=1000, check_every=1, x0=None) -> dict:
-    """Jacobi-PCG entirely in float32 on A's values rounded to float32."""
+def pcg_f32(A, bf, rtol=1e-4, max_it=1000, check_every=1, x0=None, hist_len=0, mutation=0, val32=None) -> dict:
+    """Jacobi-PCG entirely in float32 on A's values rounded to float32 (or on val32).  Returns x, iters,
+    reason, rr, bnorm and the alpha, beta and rho histories (float32 values widened to float64)."""
     rowptr, col, _ = _csr(A)
-    val32 = np.ascontiguousarray(A.val, dtype=np.float32)
+    val32 = np.ascontiguousarray(A.val if val32 is None else val32, dtype=np.float32)
     bf = np.ascontiguousarray(bf, dtype=np.float32)
     x = np.zeros(A.n, dtype=np.float32) if x0 is None else np.array(x0, dtype=np.float32, copy=True)
+    H = int(hist_len)
+    hs = {k: np.full(max(H, 1), np.nan) for k in ("alpha", "beta", "rho")}
     res = _Res()
-    load().oracle_pcg_f32(A.n, _p(rowptr), _p(col), _p(val32), _p(bf), _p(x), float(rtol), int(max_it), int(check_every), C.byref(res))
-    return dict(x=x, iters=int(res.iters), reason=REASON[res.reason], rr=float(res.rr), bnorm=float(res.bnorm))
+    load().oracle_pcg_f32(
+        A.n, _p(rowptr), _p(col), _p(val32), _p(bf), _p(x), float(rtol), int(max_it), int(check_every), H,
+        _p(hs["alpha"]), _p(hs["beta"]), _p(hs["rho"]), int(mutation), C.byref(res),
+    )
+    out = dict(x=x, iters=int(res.iters), reason=REASON[res.reason], rr=float(res.rr), bnorm=float(res.bnorm))
+    for k, v in hs.items():
+        out[k] = v[:H]
+    return out
 
 
 def ir(A, b, x0=None, rtol=1e-10, max_outer=50, rtol_inner=1e-4, max_inner=1000, inner_check_every=1, val32=None) -> dict:

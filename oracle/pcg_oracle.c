@@ -237,13 +237,28 @@ done:
   return status;
 }
 
+/* Inner product of float vectors with the products and the sum in double,
+ * rounded to float once at the end: a planted mistake (mutation 1 of the float
+ * solver), never the method. */
+static float dot_f32_in_double(int64_t n, const float* x, const float* y) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += (double)x[i] * (double)y[i];
+  return (float)s;
+}
+
 /*
  * Jacobi-PCG entirely in float: float values val32, float vectors, float
  * compensated sums.  Solves A32 xf = bf; xf holds the start on entry.
  * The stop test is sqrt(rr) <= rtol * ||bf|| (every check_every iterations).
+ * Histories as in oracle_pcg (length hist_len, may be NULL; the float values
+ * widened to double): alpha and beta of iteration i, rho = (r,z) before
+ * iteration i (rho_h[0] is the initial (r0, z0)).
+ * Planted mistakes (mutation): 1 dots accumulated in double, 2 Jacobi step
+ * dropped (z = r), 3 beta inverted, 4 wrong sign in p = z + beta p.
  */
 int oracle_pcg_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val, const float* bf, float* xf,
-                   float rtol, int32_t max_it, int32_t check_every, oracle_result* res) {
+                   float rtol, int32_t max_it, int32_t check_every, int32_t hist_len, double* alpha_h, double* beta_h,
+                   double* rho_h, int32_t mutation, oracle_result* res) {
   memset(res, 0, sizeof(*res));
   if (check_every < 1) check_every = 1;
   size_t sz = sizeof(float) * (size_t)(n > 0 ? n : 1);
@@ -262,13 +277,14 @@ int oracle_pcg_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const f
     if (!(d[i] != 0.0f)) status = OR_BAD_DIAGONAL;
   }
   if (status == OR_BAD_DIAGONAL) goto done;
+  float (*dotf)(int64_t, const float*, const float*) = (mutation == 1) ? dot_f32_in_double : dot_f32;
   oracle_spmv_f32(n, rowptr, col, val, xf, w);
   for (int64_t i = 0; i < n; ++i) r[i] = bf[i] - w[i];
-  for (int64_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
-  float rho = dot_f32(n, r, z);
+  for (int64_t i = 0; i < n; ++i) z[i] = (mutation == 2) ? r[i] : r[i] / d[i];
+  float rho = dotf(n, r, z);
   for (int64_t i = 0; i < n; ++i) p[i] = z[i];
-  float bn = sqrtf(dot_f32(n, bf, bf));
-  float rr = dot_f32(n, r, r);
+  float bn = sqrtf(dotf(n, bf, bf));
+  float rr = dotf(n, r, r);
   float tol = rtol * bn;
   res->bnorm = bn;
   res->rr = rr;
@@ -278,15 +294,17 @@ int oracle_pcg_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const f
   }
   for (int32_t it = 1; it <= max_it; ++it) {
     oracle_spmv_f32(n, rowptr, col, val, p, w);
-    float gamma = dot_f32(n, p, w);
+    float gamma = dotf(n, p, w);
+    if (it <= hist_len && rho_h) rho_h[it - 1] = (double)rho;
     if (!(gamma > 0.0f) || !isfinite(gamma)) {
       status = OR_BREAKDOWN;
       break;
     }
     float alpha = rho / gamma;
+    if (it <= hist_len && alpha_h) alpha_h[it - 1] = (double)alpha;
     for (int64_t i = 0; i < n; ++i) xf[i] += alpha * p[i];
     for (int64_t i = 0; i < n; ++i) r[i] -= alpha * w[i];
-    rr = dot_f32(n, r, r);
+    rr = dotf(n, r, r);
     res->iters = it;
     res->rr = rr;
     if (rr == 0.0f) {
@@ -301,10 +319,14 @@ int oracle_pcg_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const f
       status = OR_NOT_CONVERGED;
       break;
     }
-    for (int64_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
-    float rho_new = dot_f32(n, r, z);
-    float beta = rho_new / rho;
-    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    for (int64_t i = 0; i < n; ++i) z[i] = (mutation == 2) ? r[i] : r[i] / d[i];
+    float rho_new = dotf(n, r, z);
+    float beta = (mutation == 3) ? rho / rho_new : rho_new / rho;
+    if (it <= hist_len && beta_h) beta_h[it - 1] = (double)beta;
+    if (mutation == 4)
+      for (int64_t i = 0; i < n; ++i) p[i] = z[i] - beta * p[i];
+    else
+      for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     rho = rho_new;
   }
 done:
@@ -360,7 +382,8 @@ int oracle_ir(int64_t n, const int32_t* rowptr, const int32_t* col, const double
       df[i] = 0.0f;
     }
     oracle_result ir;
-    int st = oracle_pcg_f32(n, rowptr, col, val32, rf, df, rtol_inner, max_inner, inner_check_every, &ir);
+    int st = oracle_pcg_f32(n, rowptr, col, val32, rf, df, rtol_inner, max_inner, inner_check_every, 0, NULL, NULL,
+                            NULL, 0, &ir);
     res->inner_total += ir.iters;
     if (st == OR_BAD_DIAGONAL || st == OR_NO_MEMORY) {
       status = st;

@@ -7,7 +7,9 @@ condition-number bound), or an invariant that Jacobi-PCG must satisfy
 (D^-1-orthogonal residuals, A-conjugate steps, the Lanczos connection between
 the CG coefficients and the spectrum of D^-1 A).  The last test plants a
 mistake in the oracle (its ``mutation`` switch) and shows that at least one
-pin fails for each.
+pin fails for each; the float32 solver has its own pins (IEEE float32 rounding of a
+worked example, the float32 summation bound of the product, the refinement's
+contraction bound) and planted mistakes.
 """
 
 import math
@@ -322,6 +324,105 @@ def test_iterative_refinement_reaches_double_accuracy(orc, kind):
     assert res["outer"] >= 2  # float32 alone cannot reach 1e-10
 
 
+U32 = 2.0**-24  # unit roundoff of float32
+
+
+def test_spmv_f32_matches_scipy_within_float_bound(orc):
+    """The float32 product agrees with scipy's float64 product of the same float32 operands within the
+    float32 summation bound (m+1) 2u32 sum|a x| per row (m entries in the row)."""
+    rng = np.random.default_rng(5)
+    for A in (random_spd_csr(200, 0.05, rng), _nonsym_csr(300, 0.03, rng), diffusion_3d_27pt(6, 10.0 ** rng.uniform(-2, 2, 216))):
+        v32 = A.val.astype(np.float32)
+        x32 = rng.uniform(-1, 1, A.n).astype(np.float32)
+        y = orc.spmv_f32(A, x32)
+        assert y.dtype == np.float32
+        S = CSR(A.rowptr, A.col, v32.astype(np.float64)).to_scipy()
+        y64 = S @ x32.astype(np.float64)
+        Sabs = CSR(A.rowptr, A.col, np.abs(v32.astype(np.float64))).to_scipy()
+        m = np.diff(A.rowptr)
+        bound = (m + 1) * 2 * U32 * (Sabs @ np.abs(x32.astype(np.float64)))
+        assert np.all(np.abs(y.astype(np.float64) - y64) <= bound)
+
+
+def test_spmv_f32_rounds_every_partial_sum_to_float32(orc):
+    """Row [1, 1, 1] times x = [1, 2^-24, 2^-24]: each float32 partial sum 1 + 2^-24 is a tie and rounds
+    to 1 (ties to even), so the float32 result is exactly 1; accumulated in float64 the sum is 1 + 2^-23,
+    which float32 represents.  Terms are added in the row's stored order: [2^-24, 2^-24, 1] gives 1 + 2^-23."""
+    A3 = CSR(np.array([0, 3, 6, 7], np.int32), np.array([0, 1, 2, 2, 1, 0, 2], np.int32), np.ones(7))
+    x = np.array([1.0, 2.0**-24, 2.0**-24], np.float32)
+    y = orc.spmv_f32(A3, x)
+    assert y[0] == np.float32(1.0)
+    assert y[1] == np.float32(1.0 + 2.0**-23)
+    assert float((A3.to_scipy() @ x.astype(np.float64))[0]) == 1.0 + 2.0**-23
+
+
+def _f32_tridiag_rho0_case():
+    """3x3 tridiagonal SPD matrix with unit diagonal (D = I, so z0 = r0 = b) and b = (1 + 2^-12) (1,1,1)."""
+    e = 2.0**-4
+    A = CSR(np.array([0, 2, 5, 7], np.int32), np.array([0, 1, 0, 1, 2, 1, 2], np.int32), np.array([1, e, e, 1, e, e, 1.0]))
+    return A, np.full(3, 1 + 2.0**-12, np.float32)
+
+
+def test_f32_pcg_initial_rho_is_the_float32_value(orc):
+    """rho0 = (r0, z0) = 3 (1 + 2^-12)^2 under float32 arithmetic: each product (1 + 2^-12)^2 =
+    1 + 2^-11 + 2^-24 lies halfway between float32 neighbours and rounds to 1 + 2^-11 (ties to even); the
+    three products then add exactly to 3 + 3 2^-11.  Products or sums carried in float64 would give
+    3 + 3 2^-11 + 3 2^-24, which rounds to 3 + 3 2^-11 + 2^-22."""
+    A, b = _f32_tridiag_rho0_case()
+    res = orc.pcg_f32(A, b, rtol=0.0, max_it=1, hist_len=1)
+    assert res["rho"][0] == 3 + 3 * 2.0**-11
+
+
+def test_f32_pcg_eigenvector_rhs_alpha(orc):
+    """b = a sine mode of the 5-point Laplacian (D = 4I): one iteration with alpha1 = d / lambda, to float32
+    accuracy."""
+    N = 16
+    v = sine_mode_2d(N, 2, 3).astype(np.float32)
+    lam = lap_eig_1d(N, 2) + lap_eig_1d(N, 3)
+    res = orc.pcg_f32(laplace_2d_5pt(N), v, rtol=1e-5, max_it=50, hist_len=1)
+    assert res["iters"] == 1 and abs(res["alpha"][0] - 4.0 / lam) <= 8 * U32 * 4.0 / lam
+
+
+def test_f32_pcg_residuals_d_orthogonal(orc):
+    """The float32 iterates' true residuals are D^-1-orthogonal to float32 accuracy."""
+    rng = np.random.default_rng(42)
+    A = random_spd_csr(30, 0.2, rng, dominance=0.5)
+    A = CSR(A.rowptr, A.col, A.val.astype(np.float32).astype(np.float64))
+    Ad = A.to_dense()
+    b = rng.standard_normal(30).astype(np.float32)
+    dinv = 1.0 / np.diag(Ad)
+    rs = [b - Ad @ orc.pcg_f32(A, b, rtol=0.0, max_it=j)["x"].astype(np.float64) for j in range(4)]
+    for i in range(4):
+        for j in range(i + 1, 4):
+            den = math.sqrt(abs(rs[i] @ (dinv * rs[i])) * abs(rs[j] @ (dinv * rs[j])))
+            assert abs(rs[i] @ (dinv * rs[j])) / den < 1e-4
+
+
+@pytest.mark.parametrize("kind", ["aniso", "diffusion"])
+def test_refinement_contraction_per_correction(orc, kind):
+    """Each correction of the refinement scales the float64 true residual by at most 2 eta + 4 kappa u32
+    (eta = inner relative tolerance): the float32 rounding of r, the inner residual eta ||r|| and the
+    rounding of A's values to float32 (the standard analysis of iterative refinement, e.g. Higham,
+    Accuracy and Stability of Numerical Algorithms, Ch. 12).  So the number of corrections to reach rtol
+    is at most ceil(log(rtol) / log(2 eta + 4 kappa u32)) and, float32 alone stopping near u32 kappa, at
+    least 2 for rtol 1e-10."""
+    rng = np.random.default_rng(31)
+    if kind == "aniso":
+        A = aniso_3d_7pt_fp32exact(10, 9, 11, 1.0, 250.0, 7.0)
+    else:
+        A = diffusion_3d_27pt(9, 10.0 ** rng.uniform(-2, 2, 9**3))
+    b = rhs_from_solution(A, rng.uniform(-1, 1, A.n))
+    eta = 1e-4
+    kappa = np.linalg.cond(A.to_dense())
+    q = 2 * eta + 4 * kappa * U32
+    full = orc.ir(A, b, rtol=1e-10, rtol_inner=eta)
+    assert full["reason"] == "converged"
+    assert 2 <= full["outer"] <= math.ceil(math.log(1e-10) / math.log(q))
+    rel = [1.0] + [orc.ir(A, b, rtol=1e-10, rtol_inner=eta, max_outer=j)["rel_res"] for j in range(1, full["outer"] + 1)]
+    for k in range(full["outer"]):
+        assert rel[k + 1] <= q * rel[k]
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 
@@ -359,6 +460,46 @@ def test_pins_catch_planted_mistakes(orc):
     for m in (1, 2, 3, 4, 5, 6):
         got = _pins_pass(orc, m)
         assert not all(got.values()), f"mutation {m} went unnoticed: {got}"
+
+
+def _pins_pass_f32(orc, mutation):
+    """The float32 pins above, run against the float32 solver with a planted mistake."""
+    out = {}
+    rng = np.random.default_rng(42)
+    A = random_spd_csr(30, 0.2, rng, dominance=0.5)
+    A = CSR(A.rowptr, A.col, A.val.astype(np.float32).astype(np.float64))
+    Ad = A.to_dense()
+    b = rng.standard_normal(30).astype(np.float32)
+    xc = sla.cho_solve(sla.cho_factor(Ad), b.astype(np.float64))
+    res = orc.pcg_f32(A, b, rtol=1e-6, max_it=300, mutation=mutation)
+    err = np.linalg.norm(res["x"] - xc) / np.linalg.norm(xc)
+    out["cholesky"] = res["reason"] == "converged" and err < np.linalg.cond(Ad) * 2e-5
+    dinv = 1.0 / np.diag(Ad)
+    rs = [b - Ad @ orc.pcg_f32(A, b, rtol=0.0, max_it=j, mutation=mutation)["x"].astype(np.float64) for j in range(4)]
+    ok = True
+    for i in range(4):
+        for j in range(i + 1, 4):
+            den = math.sqrt(abs(rs[i] @ (dinv * rs[i])) * abs(rs[j] @ (dinv * rs[j]))) + 1e-300
+            ok &= abs(rs[i] @ (dinv * rs[j])) / den < 1e-4
+    out["d_orthogonal"] = bool(ok)
+    N = 16
+    v = sine_mode_2d(N, 2, 3).astype(np.float32)
+    lam = lap_eig_1d(N, 2) + lap_eig_1d(N, 3)
+    r1 = orc.pcg_f32(laplace_2d_5pt(N), v, rtol=1e-5, max_it=50, hist_len=1, mutation=mutation)
+    out["eigen_rhs"] = r1["iters"] == 1 and abs(r1["alpha"][0] - 4.0 / lam) <= 8 * U32 * 4.0 / lam
+    A3, b3 = _f32_tridiag_rho0_case()
+    out["rho0_float32"] = orc.pcg_f32(A3, b3, rtol=0.0, max_it=1, hist_len=1, mutation=mutation)["rho"][0] == 3 + 3 * 2.0**-11
+    return out
+
+
+def test_f32_pins_catch_planted_mistakes(orc):
+    """Float32 solver mistakes: dots carried in float64, the Jacobi step dropped, beta inverted, the sign of
+    the search-direction update flipped; each fails at least one float32 pin."""
+    clean = _pins_pass_f32(orc, 0)
+    assert all(clean.values()), clean
+    for m in (1, 2, 3, 4):
+        got = _pins_pass_f32(orc, m)
+        assert not all(got.values()), f"float32 mutation {m} went unnoticed: {got}"
 
 
 def test_non_finite_inputs_are_breakdowns(orc):
