@@ -466,10 +466,17 @@ APCG_API apcg_status apcg_cg_solve_host(int32_t n, int64_t nnz, const int32_t* r
  * APCG_ERR_INVALID_ARG before anything is enqueued.  Every call shares the
  * one array, which keeps the last call's contents (each call rewrites what it
  * reads): calls that overlap on the GPU -- on different streams or from
- * different host threads -- race and must not be issued.  The first call on
- * each device looks up the array's device address; make that first call
- * before any stream capture.  Returns APCG_ERR_BAD_DIAGONAL for a zero,
- * missing or non-finite diagonal entry.
+ * different host threads -- race and must not be issued.  Each call looks up
+ * the array's address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing).  The call is synchronous: it ends by waiting for the
+ * stream, so it must not be issued on a stream that is being captured.
+ *
+ * The CSR structure is checked on the device, reading rowptr[0..n] and
+ * col[0..nnz) only, before any kernel reads through it: rowptr must start at
+ * 0, never decrease and end at nnz, and every column must lie in [0, n);
+ * otherwise the call returns APCG_ERR_INVALID_ARG.  A zero, missing or
+ * non-finite diagonal entry returns APCG_ERR_BAD_DIAGONAL.  In both cases no
+ * iteration runs and x keeps its entry value.
  */
 APCG_API apcg_status apcg_cg_solve_noalloc(void* cuda_stream, int32_t n, int64_t nnz, const int32_t* rowptr,
                                            const int32_t* col, const double* val, const double* b, double* x,
@@ -500,13 +507,21 @@ typedef struct {
   int32_t max_inner;         /* inner iterations per correction (default 1000) */
   float rtol_inner;          /* inner relative tolerance (default 1e-4) */
   int32_t inner_check_every; /* inner convergence test every k iterations (default 1) */
+  /* Single-system plans: the inner alpha and beta of the FIRST correction's
+   * iterations 1..history_len (float32 values widened to double), written to
+   * these host buffers by apcg_ir_plan_solve; iterations the correction does
+   * not reach are NaN.  0 / NULL = none (default).  Batched plans ignore them. */
+  int32_t history_len;
+  int32_t pad;
+  double* alpha_hist;
+  double* beta_hist;
 } apcg_ir_opts;
 
 typedef struct {
   int32_t outer;            /* corrections applied */
   int32_t inner_total;      /* inner iterations summed over corrections */
   int32_t reason;           /* apcg_reason */
-  int32_t pad;
+  int32_t inner_first;      /* inner iterations of the first correction (single-system plans) */
   double rel_res;           /* ||b - A x|| / ||b|| at exit (float64 true residual) */
   int64_t kernel_launches;  /* kernels executed */
 } apcg_ir_result;
@@ -542,6 +557,23 @@ APCG_API apcg_status apcg_ir_plan_profile(apcg_ir_plan plan, apcg_vec b, apcg_ve
  * plan without a staged SpMV.  Blocks until the plan's graph is re-captured.
  */
 APCG_API apcg_status apcg_ir_plan_test_stall_copies(apcg_ir_plan plan, int32_t on);
+/*
+ * One application of the plan's float32 inner operator, for checking it
+ * against a plain float32 product: w = A32 p by the very kernel the inner
+ * iterations launch (the same sliced-ELL copy, column format, group size
+ * and, where the plan stages values through shared memory, the staged form),
+ * and gamma = (p, w) reduced in float32 as in the inner iteration's first
+ * step (A2-A3 of the PCG loop of Sec. 3.3, in float32).
+ *
+ * p, w: float32 device vectors of the plan's length n (caller-owned, not
+ * aliased).  gamma: host double, may be NULL.  Row i of w is the float32 sum
+ * of its entries in CSR order, each added by a fused multiply-add.  The
+ * plan's inner state is overwritten (every solve sets it up again).  Blocks
+ * until w and gamma are ready.  Errors: APCG_ERR_INVALID_ARG for a NULL, wrongly
+ * typed or wrongly sized vector; APCG_ERR_TIMEOUT if a bounded wait of the
+ * staged SpMV ran out (w is then incomplete).
+ */
+APCG_API apcg_status apcg_ir_plan_inner_spmv(apcg_ir_plan plan, apcg_vec p, apcg_vec w, double* gamma);
 APCG_API apcg_status apcg_ir_solve(apcg_ctx ctx, apcg_mat A64, apcg_mat A32, apcg_vec b, apcg_vec x,
                                    const apcg_ir_opts* opts, apcg_ir_result* res);
 
@@ -711,7 +743,10 @@ APCG_API apcg_status apcg_tfqmr_solve(apcg_ctx ctx, apcg_mat A, apcg_vec b, apcg
  * CUDA graph whose branches run concurrently.
  *
  * opts: rtol, atol, max_it (per system; <= 0 selects 10 n_s), check_every;
- * mode and history are ignored.  sys_row_off is host memory; it is copied.
+ * mode, alpha_hist and beta_hist are ignored.  history_len > 0 makes every
+ * solve record alpha and beta of iterations 1..history_len of EVERY system on
+ * the device (2 * nsys * history_len doubles of plan memory), read with
+ * apcg_batch_plan_history.  sys_row_off is host memory; it is copied.
  */
 typedef struct apcg_batch_plan_s* apcg_batch_plan;
 
@@ -752,6 +787,15 @@ APCG_API apcg_status apcg_batch_plan_solve(apcg_batch_plan plan, const double* b
  * `table` (may be NULL).  Blocks until done.
  */
 APCG_API apcg_status apcg_batch_plan_tune(apcg_batch_plan plan, const double* b, char* table, size_t cap);
+/*
+ * The alpha and beta (Sec. 3.3's CG scalars) of iterations 1..history_len of
+ * system `sys` in the last solve of a float64 batched plan created with
+ * opts.history_len > 0; iterations the system did not reach are NaN.  alpha,
+ * beta: host buffers of history_len doubles (either may be NULL).  Waits for
+ * the plan's last solve.  APCG_ERR_INVALID_ARG for a plan without history
+ * (refinement plans have none) or sys outside [0, nsys).
+ */
+APCG_API apcg_status apcg_batch_plan_history(apcg_batch_plan plan, int32_t sys, double* alpha, double* beta);
 APCG_API apcg_status apcg_batch_plan_destroy(apcg_batch_plan plan);
 
 /* One-shot form of create + solve + destroy. */

@@ -107,6 +107,10 @@ class IrOpts(C.Structure):
         ("max_inner", C.c_int32),
         ("rtol_inner", C.c_float),
         ("inner_check_every", C.c_int32),
+        ("history_len", C.c_int32),
+        ("pad", C.c_int32),
+        ("alpha_hist", C.POINTER(C.c_double)),
+        ("beta_hist", C.POINTER(C.c_double)),
     ]
 
 
@@ -115,7 +119,7 @@ class IrResult(C.Structure):
         ("outer", C.c_int32),
         ("inner_total", C.c_int32),
         ("reason", C.c_int32),
-        ("pad", C.c_int32),
+        ("inner_first", C.c_int32),
         ("rel_res", C.c_double),
         ("kernel_launches", C.c_int64),
     ]
@@ -125,6 +129,7 @@ class IrResult(C.Structure):
             "outer": int(self.outer),
             "inner_total": int(self.inner_total),
             "reason": REASONS.get(int(self.reason), int(self.reason)),
+            "inner_first": int(self.inner_first),
             "rel_res": float(self.rel_res),
             "kernel_launches": int(self.kernel_launches),
         }
@@ -238,6 +243,7 @@ PROTOS = {
     "apcg_ir_plan_layout": [P, C.POINTER(PlanLayout)],
     "apcg_ir_plan_profile": [P, P, P, i32, C.POINTER(C.c_float)],
     "apcg_ir_plan_test_stall_copies": [P, i32],
+    "apcg_ir_plan_inner_spmv": [P, P, P, C.POINTER(C.c_double)],
     "apcg_ir_solve": [P, P, P, P, P, C.POINTER(IrOpts), C.POINTER(IrResult)],
     "apcg_expr_create": [P, i32, PP],
     "apcg_expr_destroy": [P],
@@ -259,6 +265,7 @@ PROTOS = {
     "apcg_batch_ir_plan_create": [P, i32, P, P, P, P, P, C.POINTER(IrOpts), PP],
     "apcg_batch_plan_solve": [P, P, P, P],
     "apcg_batch_plan_tune": [P, P, C.c_char_p, C.c_size_t],
+    "apcg_batch_plan_history": [P, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "apcg_batch_plan_destroy": [P],
     "apcg_cg_solve_batched": [P, i32, P, P, P, P, P, P, C.POINTER(CgOpts), P],
     "apcg_sim_create": [i32, PP],
@@ -602,6 +609,13 @@ def batch_plan_create(ctx, sys_row_off, rowptr, col, val, opts: CgOpts):
     return h.value
 
 
+def batch_plan_history(plan, sys: int, history_len: int) -> dict:
+    """alpha/beta of iterations 1..history_len of system sys in the plan's last solve (NaN where not reached)."""
+    a, b = (C.c_double * history_len)(), (C.c_double * history_len)()
+    call("apcg_batch_plan_history", C.c_void_p(plan), int(sys), a, b)
+    return {"alpha": list(a), "beta": list(b)}
+
+
 def batch_plan_solve(plan, b, x, nsys: int | None = None):
     """Solve all systems; returns per-system results when nsys is given (blocks), else None (enqueued only)."""
     if nsys is None:
@@ -649,12 +663,33 @@ def cg_solve_noalloc(stream, rowptr, col, val, b, x, opts: CgOpts) -> dict:
     return res.as_dict()
 
 
-def ir_opts(rtol=1e-10, atol=0.0, max_outer=50, max_inner=1000, rtol_inner=1e-4, inner_check_every=1):
+def ir_opts(rtol=1e-10, atol=0.0, max_outer=50, max_inner=1000, rtol_inner=1e-4, inner_check_every=1, history_len=0):
     o = IrOpts()
     call("apcg_ir_opts_default", C.byref(o))
     o.rtol, o.atol, o.max_outer, o.max_inner = rtol, atol, max_outer, max_inner
     o.rtol_inner, o.inner_check_every = rtol_inner, inner_check_every
+    o.history_len = history_len
+    hist = None
+    if history_len:
+        hist = ((C.c_double * history_len)(), (C.c_double * history_len)())
+        o.alpha_hist = C.cast(hist[0], C.POINTER(C.c_double))
+        o.beta_hist = C.cast(hist[1], C.POINTER(C.c_double))
+    o._hist = hist  # keep the buffers alive with the struct (a plan keeps the pointers)
     return o
+
+
+def ir_history(opts: IrOpts) -> dict:
+    """The inner alpha/beta of the first correction written by the last solve of a plan made with opts."""
+    if not opts.history_len:
+        return {"alpha": [], "beta": []}
+    return {"alpha": list(opts._hist[0]), "beta": list(opts._hist[1])}
+
+
+def ir_plan_inner_spmv(plan, p, w) -> float:
+    """w = A32 p by the plan's float32 inner SpMV (apcg_vec handles of float32 vectors); returns (p, w)."""
+    g = C.c_double()
+    call("apcg_ir_plan_inner_spmv", C.c_void_p(plan), C.c_void_p(p), C.c_void_p(w), C.byref(g))
+    return float(g.value)
 
 
 def ir_plan_profile(plan, b, x, iters: int) -> list[float]:

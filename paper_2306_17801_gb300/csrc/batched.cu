@@ -60,6 +60,8 @@ struct apcg_batch_plan_s {
   char* ws = nullptr;
   apcg::SysDesc* d_sys = nullptr;
   apcg::SysResult* d_res = nullptr;
+  int32_t hist_len = 0;          // float64 CG: alpha/beta of the first hist_len iterations of every system
+  double* d_hist = nullptr;      // [2 * nsys * hist_len]: alpha of all systems, then beta
   apcg::SysResult* h_res = nullptr;
   cudaEvent_t start = nullptr;
   cudaGraph_t graph = nullptr;
@@ -96,7 +98,9 @@ ClusterArgs class_args(apcg_batch_plan P, const BatchClass& c, const double* b, 
   a.rtol = P->opts.rtol;
   a.atol = P->opts.atol;
   a.max_it = P->opts.max_it;
-  a.hist_len = 0;
+  a.hist_len = P->hist_len;
+  a.alpha_h = P->d_hist;
+  a.beta_h = P->d_hist ? P->d_hist + (int64_t)P->nsys * P->hist_len : nullptr;
   if (P->ir) {
     a.val32 = P->val32;
     a.rtol = P->iropts.rtol;
@@ -202,7 +206,7 @@ apcg_status create_plan(apcg_ctx ctx_in, int32_t nsys, const int32_t* sys_row_of
     o = *opts;
   else
     apcg_cg_opts_default(&o);
-  APCG_CHECK(o.check_every >= 1 && o.rtol >= 0.0 && o.atol >= 0.0, "bad options");
+  APCG_CHECK(o.check_every >= 1 && o.rtol >= 0.0 && o.atol >= 0.0 && o.history_len >= 0, "bad options");
   if (iropts) {
     APCG_CHECK(iropts->rtol >= 0.0 && iropts->atol >= 0.0 && iropts->max_outer >= 0 && iropts->max_inner >= 1 &&
                    iropts->inner_check_every >= 1 && iropts->rtol_inner >= 0.0f && iropts->rtol_inner < 1.0f,
@@ -224,6 +228,7 @@ apcg_status create_plan(apcg_ctx ctx_in, int32_t nsys, const int32_t* sys_row_of
   P->ir = iropts != nullptr;
   if (iropts) P->iropts = *iropts;
   P->opts = o;
+  P->hist_len = iropts ? 0 : o.history_len;
   P->n.resize(nsys);
   std::vector<SysDesc> desc(nsys);
   for (int32_t s = 0; s < nsys; ++s) {
@@ -254,11 +259,13 @@ apcg_status create_plan(apcg_ctx ctx_in, int32_t nsys, const int32_t* sys_row_of
   const size_t b_desc = up(sizeof(SysDesc) * nsys), b_res = up(sizeof(SysResult) * nsys);
   size_t b_cls = 0;
   for (auto& c : P->classes) b_cls += up(sizeof(int32_t) * c.sys.size()) + 256;
+  const size_t b_hist = up(sizeof(double) * 2 * (size_t)nsys * (size_t)P->hist_len);
   char* ws = nullptr;
-  APCG_TRY(dev_alloc_async((void**)&ws, b_desc + b_res + b_cls, ctx->stream));
+  APCG_TRY(dev_alloc_async((void**)&ws, b_desc + b_res + b_cls + b_hist, ctx->stream));
   P->ws = ws;
   P->d_sys = reinterpret_cast<SysDesc*>(ws);
   P->d_res = reinterpret_cast<SysResult*>(ws + b_desc);
+  if (P->hist_len > 0) P->d_hist = reinterpret_cast<double*>(ws + b_desc + b_res + b_cls);
   char* q = ws + b_desc + b_res;
   APCG_CUDA(cudaMemcpyAsync(P->d_sys, desc.data(), sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, ctx->stream));
   for (auto& c : P->classes) {
@@ -280,7 +287,7 @@ apcg_status create_plan(apcg_ctx ctx_in, int32_t nsys, const int32_t* sys_row_of
   counters().h2d_copies += 1 + (int64_t)P->classes.size();
   {
     std::lock_guard<std::mutex> g(global_mutex());
-    P->id = register_memory(ws, b_desc + b_res + b_cls);
+    P->id = register_memory(ws, b_desc + b_res + b_cls + b_hist);
   }
   *out = P.release();
   return APCG_OK;
@@ -320,6 +327,8 @@ apcg_status apcg_batch_plan_solve(apcg_batch_plan P, const double* b, double* x,
   OpScope op(P->ctx);
   op.read(idb).rw(idx).rw(P->id);
   APCG_TRY(op.begin());
+  if (P->d_hist)  // iterations a system does not reach stay NaN (all bits set)
+    APCG_CUDA(cudaMemsetAsync(P->d_hist, 0xff, sizeof(double) * 2 * (size_t)P->nsys * P->hist_len, P->ctx->stream));
   APCG_CUDA(cudaGraphLaunch(P->exec, P->ctx->stream));
   counters().graph_launches++;
   count_kernels((int64_t)P->classes.size());
@@ -416,6 +425,26 @@ apcg_status apcg_batch_plan_tune(apcg_batch_plan P, const double* b, char* table
     memcpy(table, out.data(), nb);
     table[nb] = '\0';
   }
+  return APCG_OK;
+}
+
+apcg_status apcg_batch_plan_history(apcg_batch_plan P, int32_t sys, double* alpha, double* beta) {
+  APCG_CHECK(P, "plan is NULL");
+  APCG_CHECK(P->hist_len > 0, "the plan records no history (float64 CG plans with opts.history_len > 0 only)");
+  APCG_CHECK(sys >= 0 && sys < P->nsys, "system %d outside [0, %d)", sys, P->nsys);
+  const size_t H = (size_t)P->hist_len;
+  cudaStream_t s = P->ctx->stream;
+  OpScope op(P->ctx);
+  op.read(P->id);
+  APCG_TRY(op.begin());
+  if (alpha) APCG_CUDA(cudaMemcpyAsync(alpha, P->d_hist + (size_t)sys * H, sizeof(double) * H, cudaMemcpyDeviceToHost, s));
+  if (beta)
+    APCG_CUDA(cudaMemcpyAsync(beta, P->d_hist + ((size_t)P->nsys + sys) * H, sizeof(double) * H, cudaMemcpyDeviceToHost,
+                              s));
+  APCG_TRY(op.finish());
+  APCG_CUDA(cudaStreamSynchronize(s));
+  counters().d2h_copies += (alpha ? 1 : 0) + (beta ? 1 : 0);
+  counters().host_syncs++;
   return APCG_OK;
 }
 

@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(ClusterArgs
       done = kDoneConverged;
     else
       done = clu::pcg_loop<R, double, double>(g, a.val, s_p, peer_p, xk, rk, zk, dk, v[0], rr, tol, max_it,
-                                              a.check_every, S, parity, cl, a.alpha_h, a.beta_h,
-                                              idx == 0 ? a.hist_len : 0, &it);
+                                              a.check_every, S, parity, cl, a.alpha_h + (int64_t)s * a.hist_len,
+                                              a.beta_h + (int64_t)s * a.hist_len, a.hist_len, &it);
 #pragma unroll
     for (int k = 0; k < R; ++k)
       if (clu::owns<R>(g, k)) a.x[row0 + g.lbase + threadIdx.x + k * blockDim.x] = xk[k];

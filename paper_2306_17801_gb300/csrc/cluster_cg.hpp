@@ -43,9 +43,9 @@ struct ClusterArgs {
   SysResult* res;
   double rtol, atol;
   int32_t max_it;         // CG: <= 0 means 10 n per system; refinement: inner iterations per correction
-  int32_t hist_len;       // alpha/beta history of the first system in order (CG only)
-  double* alpha_h;
-  double* beta_h;
+  int32_t hist_len;       // CG only: alpha/beta of iterations 1..hist_len of every system s, written to
+  double* alpha_h;        // alpha_h[s * hist_len + i] and beta_h[s * hist_len + i] (nullptr when hist_len
+  double* beta_h;         // is 0)
   // refinement only
   float rtol_inner;
   int32_t max_outer;

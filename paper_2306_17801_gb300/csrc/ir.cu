@@ -76,7 +76,7 @@ void ir_destroy(apcg_ir_plan P) {
 // The outer residual and the set-up of the inner solve (its tolerance rtol_inner ||r32||, at most max_inner
 // iterations).
 apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cudaStream_t s, double rtol_inner,
-                            int32_t max_inner) {
+                            int32_t max_inner, int32_t hist_len = 0) {
   ir::ResidualArgs a;
   a.n = P->n;
   a.b = b;
@@ -92,6 +92,7 @@ apcg_status launch_residual(apcg_ir_plan P, const double* b, const double* x, cu
   a.rtol_inner = rtol_inner;
   a.max_inner = max_inner;
   a.inner_k = P->core.k;
+  a.hist_len = hist_len;
   if (P->S.n > 0) {
     const int g = P->grid_res;
     switch (P->S.npts) {
@@ -155,6 +156,7 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   if (!(o.rtol_inner > 0.0f)) o.rtol_inner = 1e-4f;
   if (o.inner_check_every < 1) o.inner_check_every = 1;
   APCG_CHECK(o.rtol >= 0.0 && o.atol >= 0.0, "tolerances must be non-negative");
+  APCG_CHECK(o.history_len >= 0, "history_len must be >= 0");
   apcg_ctx ctx;
   APCG_TRY(resolve_ctx(ctx_in, &ctx));
   const apcg_mat_s& S = A64 ? *A64 : *A32;
@@ -192,7 +194,8 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   const size_t nip = up(sizeof(float) * dev::kMaxPartials * 3);
   const size_t nop = up(sizeof(double) * dev::kMaxPartials * 2);
   const size_t nst = up(sizeof(CgState)) + up(sizeof(IrState));
-  const size_t total = nsptr + ncol + nv32 + nv64 + 6 * nv + nip + nop + nst;
+  const size_t nh = up(sizeof(double) * (size_t)std::max(o.history_len, 1));
+  const size_t total = nsptr + ncol + nv32 + nv64 + 6 * nv + nip + nop + nst + 2 * nh;
   char* ws = nullptr;
   APCG_TRY(dev_alloc_async((void**)&ws, total, ctx->stream));
   P->ws = ws;
@@ -217,6 +220,8 @@ apcg_status apcg_ir_plan_create(apcg_ctx ctx_in, apcg_mat A64, apcg_mat A32, con
   P->opartials = reinterpret_cast<double*>(q + nip);
   c.st = reinterpret_cast<CgState*>(q + nip + nop);
   P->ost = reinterpret_cast<IrState*>(q + nip + nop + up(sizeof(CgState)));
+  c.alpha_h = reinterpret_cast<double*>(q + nip + nop + nst);
+  c.beta_h = reinterpret_cast<double*>(q + nip + nop + nst + nh);
   APCG_CUDA(cudaMemsetAsync(q, 0, nip + nop + nst, ctx->stream));
   APCG_CUDA(cudaMallocHost(&P->host_state, sizeof(IrState) + sizeof(CgState)));
   {
@@ -294,6 +299,7 @@ apcg_status apcg_ir_plan_create_stencil(apcg_ctx ctx_in, apcg_stencil St, const 
   if (!(o.rtol_inner > 0.0f)) o.rtol_inner = 1e-4f;
   if (o.inner_check_every < 1) o.inner_check_every = 1;
   APCG_CHECK(o.rtol >= 0.0 && o.atol >= 0.0, "tolerances must be non-negative");
+  APCG_CHECK(o.history_len >= 0, "history_len must be >= 0");
   apcg_ctx ctx;
   APCG_TRY(resolve_ctx(ctx_in, &ctx));
   std::unique_ptr<apcg_ir_plan_s, void (*)(apcg_ir_plan)> P(new apcg_ir_plan_s(), ir_destroy);
@@ -319,7 +325,8 @@ apcg_status apcg_ir_plan_create_stencil(apcg_ctx ctx_in, apcg_stencil St, const 
   const size_t nip = up(sizeof(float) * dev::kMaxPartials * 3);
   const size_t nop = up(sizeof(double) * dev::kMaxPartials * 2);
   const size_t nst = up(sizeof(CgState)) + up(sizeof(IrState));
-  const size_t total = 6 * nv + nip + nop + nst;
+  const size_t nh = up(sizeof(double) * (size_t)std::max(o.history_len, 1));
+  const size_t total = 6 * nv + nip + nop + nst + 2 * nh;
   char* ws = nullptr;
   APCG_TRY(dev_alloc_async((void**)&ws, total, ctx->stream));
   P->ws = ws;
@@ -334,6 +341,8 @@ apcg_status apcg_ir_plan_create_stencil(apcg_ctx ctx_in, apcg_stencil St, const 
   P->opartials = reinterpret_cast<double*>(q + nip);
   c.st = reinterpret_cast<CgState*>(q + nip + nop);
   P->ost = reinterpret_cast<IrState*>(q + nip + nop + up(sizeof(CgState)));
+  c.alpha_h = reinterpret_cast<double*>(q + nip + nop + nst);
+  c.beta_h = reinterpret_cast<double*>(q + nip + nop + nst + nh);
   APCG_CUDA(cudaMemsetAsync(q, 0, nip + nop + nst, ctx->stream));
   APCG_CUDA(cudaMallocHost(&P->host_state, sizeof(IrState) + sizeof(CgState)));
   {
@@ -373,8 +382,14 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
   memset(res, 0, sizeof(*res));
   int64_t launches = 0;
   apcg_status st = APCG_OK;
-  for (int32_t k = 0;; ++k) {
-    st = launch_residual(P, bp, xp, s, P->opts.rtol_inner, P->core.max_it);
+  const int32_t H = P->opts.history_len;
+  if (H > 0) {  // entries the first correction does not reach stay NaN (all bits set)
+    cudaError_t e = cudaMemsetAsync(P->core.alpha_h, 0xff, sizeof(double) * H, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->core.beta_h, 0xff, sizeof(double) * H, s);
+    if (e != cudaSuccess) st = cuda_error(e, "history reset", __FILE__, __LINE__);
+  }
+  for (int32_t k = 0; st == APCG_OK; ++k) {
+    st = launch_residual(P, bp, xp, s, P->opts.rtol_inner, P->core.max_it, k == 0 ? H : 0);
     if (st != APCG_OK) break;
     launches += 1;
     cudaError_t e = cudaMemcpyAsync(ho, P->ost, sizeof(IrState), cudaMemcpyDeviceToHost, s);
@@ -427,6 +442,7 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
     }
     counters().d2h_copies++;
     res->inner_total += hi->iter;
+    if (k == 0) res->inner_first = hi->iter;
     launches += (int64_t)hi->body_runs * 3 * P->core.k;
     res->outer = k + 1;
     if (hi->done == kDoneTimeout) {  // a bounded wait in the staged SpMV ran out: the correction is not usable
@@ -435,10 +451,57 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
       break;
     }
   }
+  if (st == APCG_OK && H > 0 && (P->opts.alpha_hist || P->opts.beta_hist)) {
+    cudaError_t e = cudaSuccess;
+    if (P->opts.alpha_hist)
+      e = cudaMemcpyAsync(P->opts.alpha_hist, P->core.alpha_h, sizeof(double) * H, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && P->opts.beta_hist)
+      e = cudaMemcpyAsync(P->opts.beta_hist, P->core.beta_h, sizeof(double) * H, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_error(e, "history read", __FILE__, __LINE__);
+    counters().d2h_copies += 2;
+    counters().host_syncs++;
+  }
   res->kernel_launches = launches;
   count_kernels(launches);
   apcg_status st2 = op.finish();
   return st != APCG_OK ? st : st2;
+}
+
+apcg_status apcg_ir_plan_inner_spmv(apcg_ir_plan P, apcg_vec p32, apcg_vec w32, double* gamma) {
+  APCG_CHECK(P && p32 && w32, "NULL argument");
+  APCG_CHECK(p32->dtype == APCG_F32 && w32->dtype == APCG_F32, "p and w must be float32");
+  APCG_CHECK(p32->n == P->n && w32->n == P->n, "p/w length differs from the matrix size %d", P->n);
+  APCG_CHECK(p32->dptr != w32->dptr || P->n == 0, "p and w must not alias");
+  if (gamma) *gamma = 0.0;
+  if (P->n == 0) return APCG_OK;
+  cudaStream_t s = P->ctx->stream;
+  OpScope op(P->ctx);
+  op.read(P->id_a64).read(P->id_a32).read(p32->id).write(w32->id).rw(P->id);
+  APCG_TRY(op.begin());
+  // the inner solve's K1 instance, reading p32 and writing w32 in place of the plan's p and w; a cleared
+  // state block (not done, no history, ticket 0) so that it runs its whole sweep and its last block only
+  // forms gamma and alpha in the state
+  CgCore<float> c = P->core;
+  c.p = static_cast<float*>(p32->dptr);
+  c.w = static_cast<float*>(w32->dptr);
+  APCG_CUDA(cudaMemsetAsync(c.st, 0, sizeof(CgState), s));
+  apcg_status st = core_k1(c, P->d32, s, false);
+  count_kernels(1);
+  CgState hs;
+  if (st == APCG_OK) {
+    cudaError_t e = cudaMemcpyAsync(P->host_state, c.st, sizeof(CgState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_error(e, "state read", __FILE__, __LINE__);
+    memcpy(&hs, P->host_state, sizeof(hs));
+    counters().d2h_copies++;
+    counters().host_syncs++;
+  }
+  apcg_status st2 = op.finish();
+  APCG_TRY(st);
+  if (hs.done == kDoneTimeout) return set_error(APCG_ERR_TIMEOUT, "a bounded device wait ran out (staged float32 SpMV)");
+  if (gamma) *gamma = hs.gamma;
+  return st2;
 }
 
 apcg_status apcg_ir_plan_profile(apcg_ir_plan P, apcg_vec b, apcg_vec x, int32_t iters, float* ms) {

@@ -54,6 +54,7 @@ struct ResidualArgs {
   float* ipartials;   // [2 * kMaxPartials] (the inner core's partials)
   float rtol_inner;
   int32_t max_inner, inner_k;
+  int32_t hist_len;   // inner alpha/beta to record in this correction (the core's history arrays)
 };
 
 // r = b - A x in float64 (values TV widened to double), ||r||^2 and ||b||^2 in
@@ -95,7 +96,7 @@ __device__ __forceinline__ void residual_body(const ResidualArgs& a, Spmv spmv) 
     st->iter = 0;
     st->max_it = a.max_inner;
     st->check_every = a.inner_k;
-    st->hist_len = 0;
+    st->hist_len = a.hist_len;
     st->body_runs = 0;
     st->alpha = st->beta = st->gamma = st->rho_new = 0.0;
     st->done = (sqrtf(t32[1]) <= tol) ? kDoneConverged : 0;

@@ -43,26 +43,40 @@ def _dev(B: Batch, x0=None):
     return t(B.rowptr), t(B.col), t(B.val), t(B.b), x
 
 
-def _solve(ctx, B, rtol=1e-8, k=1, tune=False, max_it=0):
+H = 10  # alpha/beta of the first H iterations of every system are recorded and compared
+
+
+def _solve(ctx, B, rtol=1e-8, k=1, tune=False, max_it=0, hist=H):
     rowptr, col, val, b, x = _dev(B)
-    opts = apcg.cg_opts(rtol=rtol, check_every=k, max_it=max_it)
+    opts = apcg.cg_opts(rtol=rtol, check_every=k, max_it=max_it, history_len=hist)
     plan = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, val, opts)
     table = apcg.batch_plan_tune(plan, b) if tune else None
     res = apcg.batch_plan_solve(plan, b, x, B.nsys)
+    if hist:
+        for s in range(B.nsys):
+            res[s].update(apcg.batch_plan_history(plan, s, hist))
     apcg.call("apcg_batch_plan_destroy", C.c_void_p(plan))
     return res, x.cpu().numpy(), table
 
 
 def _check_system(B, s, res_s, xg, rtol, k):
+    """One system of a batch against the oracle: reason, count within the test cadence, alpha/beta of the
+    first iterations within 1e-12 relative, and x within 1e-7 of the oracle's iterate at the GPU's count."""
     A, b, _ = B.system(s)
     r0, r1 = int(B.sys_row_off[s]), int(B.sys_row_off[s + 1])
-    ref = oracle.pcg(A, b, rtol=rtol, check_every=k)
+    ref = oracle.pcg(A, b, rtol=rtol, check_every=k, hist_len=H)
     assert res_s["reason"] == ref["reason"] == "converged", (s, res_s, ref["reason"])
     assert abs(res_s["iters"] - ref["iters"]) <= k, (s, res_s["iters"], ref["iters"])
     assert res_s["rel_res"] <= rtol
-    if res_s["iters"] == ref["iters"]:
-        err = np.linalg.norm(xg[r0:r1] - ref["x"]) / np.linalg.norm(ref["x"])
-        assert err <= 1e-7, (s, err)
+    if "alpha" in res_s:
+        h = min(H, ref["iters"] - 1, res_s["iters"] - 1)
+        for key in ("alpha", "beta"):
+            g = np.array(res_s[key][:h])
+            err = float(np.max(np.abs(g - ref[key][:h]) / np.abs(ref[key][:h]))) if h > 0 else 0.0
+            assert err <= 1e-12, (s, key, err)
+    x_ref = ref["x"] if res_s["iters"] == ref["iters"] else oracle.pcg(A, b, rtol=0.0, max_it=res_s["iters"])["x"]
+    err = np.linalg.norm(xg[r0:r1] - x_ref) / np.linalg.norm(x_ref)
+    assert err <= 1e-7, (s, err)
 
 
 @pytest.mark.parametrize("k", [1, 4])

@@ -80,6 +80,15 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 
 
+def _oracle_x_at(A, b, ref, iters):
+    """The oracle's iterate after exactly `iters` iterations: its converged x when it stopped there too,
+    else a rerun without a tolerance and capped at that count (near the threshold rounding may move the
+    stop by one test block, so the solutions are compared at the GPU's count)."""
+    if ref["iters"] == iters:
+        return ref["x"]
+    return oracle.pcg(A, b, rtol=0.0, max_it=iters)["x"]
+
+
 def _ragged_nonsym(n, rng):
     """Rows of very different lengths: empty rows, short rows, one long row."""
     lens = rng.integers(0, 12, n)
@@ -247,8 +256,8 @@ def test_cg_parity_ragged_sizes(dev, ctx, name, size, k, mode):
     h = min(10, ref["iters"] - 1)
     assert np.max(np.abs(np.array(res["alpha"][:h]) - ref["alpha"][:h]) / np.abs(ref["alpha"][:h])) <= 1e-12
     assert np.max(np.abs(np.array(res["beta"][:h]) - ref["beta"][:h]) / np.abs(ref["beta"][:h])) <= 1e-12
-    if res["iters"] == ref["iters"]:
-        assert _rel(d.x.cpu().numpy(), ref["x"]) <= 1e-7
+    # x against the oracle's iterate at the GPU's own count (the counts may differ by a test block)
+    assert _rel(d.x.cpu().numpy(), _oracle_x_at(p.A, p.b, ref, res["iters"])) <= 1e-7
     assert res["rel_res"] <= 1e-8
     d.close()
 
@@ -351,8 +360,7 @@ def test_cg_c2_full_size_parity(dev, ctx):
     assert abs(res["iters"] - ref["iters"]) <= 10
     assert np.max(np.abs(np.array(res["alpha"]) - ref["alpha"]) / np.abs(ref["alpha"])) <= 1e-12
     assert np.max(np.abs(np.array(res["beta"]) - ref["beta"]) / np.abs(ref["beta"])) <= 1e-12
-    if res["iters"] == ref["iters"]:
-        assert _rel(d.x.cpu().numpy(), ref["x"]) <= 1e-7
+    assert _rel(d.x.cpu().numpy(), _oracle_x_at(p.A, p.b, ref, res["iters"])) <= 1e-7
     # true residual of the GPU solution
     x = d.x.cpu().numpy()
     assert np.linalg.norm(p.b - oracle.spmv(p.A, x)) / np.linalg.norm(p.b) <= 2e-8
