@@ -11,6 +11,18 @@ the same work as the paper's timed KSPSolve (Sec. 4.1).  Inputs are resident
 in HBM when the timed region starts; the working set (CSR 175 MB plus five
 16.8 MB vectors) is larger than L2, so no flush is needed between steps.
 
+Beside the headline, rank 0 adds to the same JSON line (unless --no-extra):
+the host-synchronous and launch-per-kernel forms (minimum of repeated
+solves), the 64^2 small case and launch floor, the measured float64 FMA
+peak, the CPU oracle on all host cores and on one, and one block per further
+workload -- c3 (160^3 variable-coefficient 27-point: float64 PCG against the
+float32-inner refinement to rtol 1e-10), c4 (1024 shifted 5-point systems:
+one batched launch against one system at a time), c5 (4096 anisotropic
+7-point systems: batched refinement against float64 one system at a time)
+and tfqmr (Jacobi-TFQMR on the 128^3 system) -- each with its speed-up, its
+error against the float64 oracle and a roofline over algorithmic and stored
+bytes.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl apcg|reference]
 Under torchrun every rank solves its own replica (replicas only: a single
 solve is not sharded), value = total solves / max-over-ranks time.
@@ -131,28 +143,54 @@ def _traffic_record():
         return None
 
 
+def _config(n, nnz, world):
+    """The workload description both arms print (same keys, same values)."""
+    return {
+        "workload": WORKLOAD,
+        "n": n,
+        "nnz": nnz,
+        "rtol": RTOL,
+        "check_every": K_CHECK,
+        "parallelism": "replicas" if world > 1 else "single",
+        "l2": "inputs larger than L2 (CSR 175 MB + 5 x 16.8 MB vectors), no flush",
+    }
+
+
 def run_reference(args, rank, world):
-    """The CPU oracle, as it stands, on a bounded sample of the same workload."""
+    """The CPU oracle on the host cores: each step one complete solve of the benchmark system to rtol 1e-8
+    by the multi-threaded variant of the float64 oracle (every core of this process's affinity mask); where
+    gcc has no OpenMP, the single-threaded oracle on a 20-iteration sample per step."""
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
     from synthetic import single_problem
 
     p = single_problem("c2", seed=0)
-    iters_full = _golden_iters()
-    sample_iters = 20  # the paper's fixed-iteration solve (Sec. 4.1)
-    times = []
+    cores, model = oracle.host_cores(), oracle.host_cpu_model()
+    omp = oracle.build_omp() is not None
+    times, iters = [], None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = oracle.pcg(p.A, p.b, rtol=0.0, max_it=sample_iters, check_every=K_CHECK)
+        if omp:
+            r = oracle.pcg_omp(p.A, p.b, rtol=RTOL, max_it=MAX_IT, check_every=K_CHECK, threads=cores)
+            assert r["reason"] == "converged", r["reason"]
+        else:
+            r = oracle.pcg(p.A, p.b, rtol=0.0, max_it=20, check_every=K_CHECK)
         dt = time.perf_counter() - t0
-        assert r["iters"] == sample_iters
+        iters = r["iters"]
         if i >= args.warmup:
             times.append(dt)
-    t_iter = sum(times) / (len(times) * sample_iters)
-    value = 1.0 / (t_iter * iters_full)
+    ms_step = 1e3 * sum(times) / len(times)
+    if omp:
+        value = 1e3 / ms_step
+        sample = f"complete solves to rtol {RTOL:g} ({iters} iterations), one per step, OpenMP over {cores} cores"
+        per_solve = ms_step
+    else:
+        iters_full = _golden_iters()
+        value = 1e3 / (ms_step / iters * iters_full)
+        sample = (f"{iters} PCG iterations of the 128^3 system per step (single-threaded; no OpenMP), solves/s "
+                  f"scaled by the {iters_full} iterations of a full solve")
+        per_solve = ms_step / iters * iters_full
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -161,31 +199,27 @@ def run_reference(args, rank, world):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_iter * iters_full,
-        "us_per_iteration": 1e6 * t_iter,
+        "ms_per_step": ms_step,
+        "ms_per_solve": per_solve,
+        "us_per_iteration": 1e3 * ms_step / iters,
+        "iters_per_step": iters,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "iters_per_solve": iters_full},
-        "cpu_baseline": {
-            "value": value,
-            "unit": "solves/s",
-            "cores": 1,
-            "kind": "oracle",
-            "sample": f"{sample_iters} PCG iterations of the full 128^3 system per step (single-threaded C), "
-            f"scaled by the {iters_full} iterations of a full solve",
-        },
+        "config": _config(p.n, p.nnz, world),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores if omp else 1, "cpu_model": model,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
-    _ = np
 
 
 def cpu_baseline_sample():
-    """Time the oracle on a bounded sample (about 10 s of CPU work) of the workload."""
+    """The float64 oracle on this host: one complete solve by the multi-threaded variant on every core of
+    the affinity mask (the value), and the single-threaded oracle on a 150-iteration sample."""
     import oracle
     from synthetic import single_problem
 
@@ -197,15 +231,50 @@ def cpu_baseline_sample():
     dt = time.perf_counter() - t0
     assert r["iters"] == sample_iters
     t_iter = dt / sample_iters
-    return {
-        "value": 1.0 / (t_iter * iters_full),
-        "unit": "solves/s",
-        "cores": 1,
-        "kind": "oracle",
-        "sample": f"{sample_iters} PCG iterations of the full 128^3 system (single-threaded C oracle), "
-        f"scaled by the {iters_full} iterations of a full solve",
+    single = {
+        "value": 1.0 / (t_iter * iters_full), "unit": "solves/s", "cores": 1, "sampled_s": dt,
         "us_per_iteration": 1e6 * t_iter,
+        "sample": f"{sample_iters} PCG iterations of the 128^3 system ({dt:.2f} s, single-threaded C oracle), "
+                  f"scaled by the {iters_full} iterations of a full solve",
     }
+    cores, model = oracle.host_cores(), oracle.host_cpu_model()
+    if oracle.build_omp() is None:
+        return {**single, "kind": "oracle", "cpu_model": model, "note": "gcc without OpenMP: single core only"}
+    oracle.pcg_omp(p.A, p.b, rtol=0.0, max_it=10, check_every=K_CHECK, threads=cores)  # warm the pages
+    t0 = time.perf_counter()
+    r = oracle.pcg_omp(p.A, p.b, rtol=RTOL, max_it=MAX_IT, check_every=K_CHECK, threads=cores)
+    dt = time.perf_counter() - t0
+    assert r["reason"] == "converged"
+    return {
+        "value": 1.0 / dt, "unit": "solves/s", "cores": cores, "cpu_model": model, "kind": "oracle",
+        "sample": f"one complete solve to rtol {RTOL:g} ({r['iters']} iterations, {dt:.2f} s) by the float64 "
+                  f"oracle's steps split over {cores} OpenMP threads",
+        "us_per_iteration": 1e6 * dt / r["iters"], "single_thread": single,
+    }
+
+
+def _col_bytes(lay):
+    """Bytes of column information per stored entry of a plan's sliced-ELL copy, by column format."""
+    return {"pattern": 4.0 / 32.0, "offset16": 2.0, "index": 4.0}.get(lay["col_format"], 4.0)
+
+
+def _stored_spmv_bytes(lay, vsize):
+    """Bytes one sweep of the plan's sliced-ELL SpMV streams: values, column information, slice offsets."""
+    return vsize * lay["padded"] + _col_bytes(lay) * lay["padded"] + 4 * (lay["nslices"] + 1)
+
+
+def _roofline(bytes_alg, bytes_stored, seconds, peak, kind):
+    """A roofline entry over both byte counts; frac is over the stored bytes (what the kernels move)."""
+    st = bytes_stored / seconds / 1e9
+    return {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": kind, "algorithmic_bytes": bytes_alg,
+            "stored_bytes": bytes_stored, "achieved": st, "frac": st / peak,
+            "algorithmic_GBps": bytes_alg / seconds / 1e9}
+
+
+def _rel_err(a, b):
+    import numpy as np
+
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 def run_apcg(args, rank, world, local):
@@ -272,9 +341,12 @@ def run_apcg(args, rank, world, local):
     ms_step = ms_total / args.steps
     it = iters[-1]
     gpu_launches = c1["kernel_launches"] - c0["kernel_launches"]
+    x_gpu = x.cpu().numpy()
 
     out = {}
     if rank == 0:
+        peak, peak_kind = _peaks()
+        lay = apcg.plan_layout(plan, "cg")
         # ---- dominant kernel: SpMV + (p,Ap), timed alone on the same stream
         prof_plan = make_plan("async")
         apcg.call("apcg_vec_set_async", V(ctx), V(vx), C.c_double(0.0))
@@ -283,9 +355,11 @@ def run_apcg(args, rank, world, local):
         bytes_k1 = 12 * nnz + 4 * (n + 1) + 16 * n
         bytes_k2, bytes_k3 = 64 * n, 24 * n  # K2: read x,r,p,w,dinv write x,r,z; K3: read p,z write p
         bytes_iter = 12 * nnz + 4 * (n + 1) + 104 * n
-        peak, peak_kind = _peaks()
+        stored_k1 = _stored_spmv_bytes(lay, 8) + 16 * n
         ach = bytes_k1 / (ms_k[0] * 1e-3) / 1e9
         trec = _traffic_record()
+        fp64_peak = apcg.fp64_fma_peak(ctx, 5)
+        fl_k1 = 2.0 * (nnz + n) / (ms_k[0] * 1e-3) / 1e9
         out["roofline"] = {
             "kernel": "k1_kernel: SpMV w = A p with (p,w) and alpha (sliced-ELL, float64)",
             "bound": "hbm",
@@ -296,13 +370,17 @@ def run_apcg(args, rank, world, local):
             "frac": ach / peak,
             "traffic": trec["traffic_bytes_per_launch"] if trec else None,
             "algorithmic_bytes": bytes_k1,
+            "stored_bytes": stored_k1,
+            "stored_GBps": stored_k1 / (ms_k[0] * 1e-3) / 1e9,
+            "layout": lay,
             "avg_launch_ms": ms_k[0],
             # the second bound of this kernel on GB300: one float64 FMA per stored entry and per row for (p,w)
             "fp64": {
-                "achieved_gflops": 2.0 * (nnz + n) / (ms_k[0] * 1e-3) / 1e9,
-                "peak_gflops": 1257.0,
-                "peak_kind": "nominal: 2 float64 FMA lanes per SM per cycle x 152 SMs x 2.07 GHz",
-                "frac": 2.0 * (nnz + n) / (ms_k[0] * 1e-3) / 1e9 / 1257.0,
+                "achieved_gflops": fl_k1,
+                "peak_gflops": fp64_peak,
+                "peak_kind": "measured: independent float64 FMA chains on every SM (apcg_fp64_fma_peak)",
+                "frac": fl_k1 / fp64_peak,
+                "stored_fma_frac": 2.0 * (lay["padded"] + n) / (ms_k[0] * 1e-3) / 1e9 / fp64_peak,
             },
         }
         us_iter = 1e3 * ms_step / it
@@ -317,19 +395,31 @@ def run_apcg(args, rank, world, local):
             "algorithmic_bytes_per_iteration": bytes_iter,
             "GBps_per_iteration": bytes_iter / (us_iter * 1e-6) / 1e9,
             "frac_of_peak": bytes_iter / (us_iter * 1e-6) / 1e9 / peak,
+            "stored_bytes_per_iteration": stored_k1 + bytes_k2 + bytes_k3,
+            "stored_frac_of_peak": (stored_k1 + bytes_k2 + bytes_k3) / (us_iter * 1e-6) / 1e9 / peak,
         }
-        # ---- host-synchronous and launch-per-kernel forms of the same solve
+        # ---- host-synchronous and launch-per-kernel forms of the same solve: minimum over repeated solves
+        # (the paper's method, Sec. 4.1), CUDA events on the context stream
         modes = {}
+        reps = max(5, args.steps // 4)
         for mode in ("host_sync", "async"):
             pl = make_plan(mode)
             step(pl)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = step(pl)
-            dt = time.perf_counter() - t0
-            modes[mode] = {"ms_per_solve": 1e3 * dt, "us_per_iteration": 1e6 * dt / r["iters"], "iters": r["iters"]}
+            best = None
+            for _ in range(reps):
+                apcg.call("apcg_vec_set_async", V(ctx), V(vx), C.c_double(0.0))
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                r = apcg.cg_plan_solve(pl, vb, vx)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                best = f0.elapsed_time(f1) if best is None else min(best, f0.elapsed_time(f1))
+            modes[mode] = {"ms_per_solve": best, "us_per_iteration": 1e3 * best / r["iters"], "iters": r["iters"],
+                           "solves_timed": reps, "statistic": "minimum"}
             apcg.call("apcg_cg_plan_destroy", V(pl))
-        modes["async_graph"] = {"ms_per_solve": ms_step, "us_per_iteration": us_iter, "iters": it}
+        modes["async_graph"] = {"ms_per_solve": ms_step, "us_per_iteration": us_iter, "iters": it,
+                                "solves_timed": args.steps, "statistic": "mean of the timed region"}
         modes["speedup_async_graph_vs_host_sync"] = modes["host_sync"]["us_per_iteration"] / us_iter
         out["modes"] = modes
         # ---- end to end through the host-buffer entry point (pinned host memory)
@@ -362,11 +452,28 @@ def run_apcg(args, rank, world, local):
             assert rr.reason == 0
             h2d = sum(v.numel() * v.element_size() for v in hp.values()) + xh.numel() * 8
             out["e2e"] = {"value": 1.0 / dt, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 8, "ms_per_step": 1e3 * dt}
-        # ---- the oracle on the host cores
+        # ---- the oracle on the host cores, and the headline solution against the float64 oracle
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_sample()
+        out["accuracy"] = _c2_accuracy(p, x_gpu)
         # ---- the small case: 64^2 5-point, host-sync vs async forms (k = 1)
         out["small_case"] = small_case(apcg, ctx, dev)
+        # ---- the further workloads of the method: mixed precision, batches, TFQMR
+        if not args.no_extra:
+            for h, fn in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (A, "apcg_mat_destroy")):
+                apcg.call(fn, V(h))
+            apcg.call("apcg_cg_plan_destroy", V(plan))
+            del rowptr, col, val, b
+            x_ref64 = out["accuracy"].pop("_x_oracle", None)
+            out["tfqmr"] = tfqmr_block(apcg, ctx, stream, dev, p, x_ref64, peak, peak_kind, c2_only=True)
+            del p
+            torch.cuda.empty_cache()
+            out["c3"] = c3_block(apcg, ctx, stream, dev, peak, peak_kind)
+            torch.cuda.empty_cache()
+            out["c4"] = c4_block(apcg, ctx, stream, dev, tune=not args.no_tune)
+            torch.cuda.empty_cache()
+            out["c5"] = c5_block(apcg, ctx, stream, dev, tune=not args.no_tune)
+        out.get("accuracy", {}).pop("_x_oracle", None)
 
     if rank == 0:
         line = {
@@ -384,14 +491,8 @@ def run_apcg(args, rank, world, local):
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic",
-            "config": {
-                "workload": WORKLOAD,
-                "n": n,
-                "nnz": nnz,
-                "mode": "async_graph",
-                "parallelism": "replicas" if world > 1 else "single",
-                "l2": "inputs larger than L2 (CSR 175 MB + 5 x 16.8 MB vectors), no flush",
-            },
+            "solver_mode": "async_graph",
+            "config": _config(n, nnz, world),
             "clocks": clk.summary(),
             "gpu_launches": gpu_launches,
             **out,
@@ -400,6 +501,21 @@ def run_apcg(args, rank, world, local):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _c2_accuracy(p, x_gpu):
+    """The headline solution against the float64 oracle's (its multi-threaded variant, same steps) and x_true."""
+    import oracle
+
+    out = {"rel_err_vs_x_true": _rel_err(x_gpu, p.x_true) if getattr(p, "x_true", None) is not None else None}
+    if oracle.build_omp() is None:
+        out["note"] = "gcc without OpenMP: no float64 oracle solve of the full system in the benchmark"
+        return out
+    r = oracle.pcg_omp(p.A, p.b, rtol=RTOL, max_it=MAX_IT, check_every=K_CHECK, threads=oracle.host_cores())
+    out["rel_err_vs_fp64_oracle"] = _rel_err(x_gpu, r["x"])
+    out["oracle_iters"] = r["iters"]
+    out["_x_oracle"] = r["x"]
+    return out
 
 
 def small_case(apcg, ctx, dev):
@@ -456,6 +572,7 @@ def main():
     ap.add_argument("--config", choices=["c2", "c3", "c4", "c5", "tfqmr", "stencil"], default="c2",
                     help="c2: the headline 128^3 workload (default); c3/c4/c5/tfqmr/stencil: extra measurement lines")
     ap.add_argument("--no-tune", action="store_true", help="c4/c5: skip the batched autotuner")
+    ap.add_argument("--no-extra", action="store_true", help="headline only: no c3/c4/c5/tfqmr blocks")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
@@ -475,8 +592,11 @@ def main():
     if args.ncu_case:
         ncu_case(args.ncu_case)
         return
+    if args.config == "stencil":
+        bench_stencil(args)
+        return
     if args.config != "c2":
-        {"c3": bench_c3, "c4": bench_c4, "c5": bench_c5, "tfqmr": bench_tfqmr, "stencil": bench_stencil}[args.config](args)
+        _standalone(args, args.config)
         return
     run_apcg(args, rank, world, local)
 
@@ -495,115 +615,155 @@ def _gpu_problem(p, dev):
     return d
 
 
-def bench_c3(args):
-    """160^3 variable-coefficient 27-point: float64 PCG vs float32-inner refinement, both to rtol 1e-10."""
-    import ctypes as C
-
+def _timed_solves(stream, reset, fn, reps):
+    """Minimum over `reps` solves (after one untimed) of CUDA-event time on the context stream, and the last
+    result."""
     import torch
 
-    from paper_2306_17801_gb300 import apcg
+    best, r = None, None
+    for i in range(reps + 1):
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+    return best, r
+
+
+def _oracle_sample(jobs):
+    """Run oracle solves (callables) on the host cores; ctypes releases the GIL during each C call."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, oracle.host_cores())) as ex:
+        return list(ex.map(lambda f: f(), jobs))
+
+
+def c3_block(apcg, ctx, stream, dev, peak, peak_kind, reps=3):
+    """160^3 variable-coefficient 27-point to rtol 1e-10: float64 PCG (graph mode) against the float32-inner
+    refinement; both solutions against the float64 oracle's."""
+    import ctypes as C
+
+    import oracle
     from synthetic import single_problem
 
     V = C.c_void_p
-    dev = torch.device("cuda", 0)
-    apcg.load()
     p = single_problem("c3", seed=0)
     n, nnz = p.n, p.nnz
     g = _gpu_problem(p, dev)
-    stream = torch.cuda.Stream(device=dev)
-    ctx = apcg.ctx_create(stream)
-    out = {"config": {"workload": "3D 27-point variable-kappa diffusion 160^3 (n=4,096,000, nnz=109,215,352), rtol 1e-10"}}
-
-    def timed(fn, reps):
-        best, r = None, None
-        for i in range(reps + 1):
-            apcg.call("apcg_vec_set_async", V(ctx), V(g["vx"]), C.c_double(0.0))
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            if i > 0:
-                best = ms if best is None else min(best, ms)
-        return best, r
-
+    reset = lambda: apcg.call("apcg_vec_set_async", V(ctx), V(g["vx"]), C.c_double(0.0))  # noqa: E731
+    out = {"workload": "3D 27-point variable-kappa diffusion 160^3 (n=4,096,000, nnz=109,215,352), rtol 1e-10"}
     plan = apcg.cg_plan_create(ctx, g["A"], apcg.cg_opts(rtol=1e-10, check_every=10, mode="async_graph", max_it=50000))
-    ms64, r64 = timed(lambda: apcg.cg_plan_solve(plan, g["vb"], g["vx"]), max(1, args.steps // 3))
-    k64 = apcg.cg_plan_profile(plan, g["vb"], g["vx"], 5)  # after the timed solves: x is overwritten
+    ms64, r64 = _timed_solves(stream, reset, lambda: apcg.cg_plan_solve(plan, g["vb"], g["vx"]), reps)
+    x64 = g["x"].cpu().numpy()
+    k64 = apcg.cg_plan_profile(plan, g["vb"], g["vx"], 5)
     lay64 = apcg.plan_layout(plan, "cg")
     apcg.call("apcg_cg_plan_destroy", V(plan))
-    b_it64 = 12 * nnz + 4 * (n + 1) + 104 * n
-    b_k1_64 = 12 * nnz + 4 * (n + 1) + 16 * n
-    out["fp64_pcg"] = {
-        "ms_per_solve": ms64, "iters": r64["iters"], "us_per_iteration": 1e3 * ms64 / r64["iters"],
-        "GBps_per_iteration": b_it64 / (1e-3 * ms64 / r64["iters"]) / 1e9, "rel_res": r64["rel_res"],
-        "kernel_ms": dict(zip(("spmv_dot", "update", "aypx"), k64)), "spmv_GBps": b_k1_64 / (1e-3 * k64[0]) / 1e9,
-        "layout": lay64,
-    }
     irp = apcg.ir_plan_create(ctx, g["A"], None, apcg.ir_opts(rtol=1e-10, rtol_inner=1e-4, inner_check_every=10))
-    msir, rir = timed(lambda: apcg.ir_plan_solve(irp, g["vb"], g["vx"]), max(1, args.steps // 3))
+    msir, rir = _timed_solves(stream, reset, lambda: apcg.ir_plan_solve(irp, g["vb"], g["vx"]), reps)
+    xir = g["x"].cpu().numpy()
     kir = apcg.ir_plan_profile(irp, g["vb"], g["vx"], 5)
     layir = apcg.plan_layout(irp, "ir")
     apcg.call("apcg_ir_plan_destroy", V(irp))
-    b_it32 = 8 * nnz + 4 * (n + 1) + 52 * n
-    b_k1_32 = 8 * nnz + 4 * (n + 1) + 8 * n
-    out["mixed_ir"] = {
-        "ms_per_solve": msir, "outer": rir["outer"], "inner_total": rir["inner_total"],
-        "us_per_inner_iteration": 1e3 * msir / max(1, rir["inner_total"]),
-        "GBps_per_inner_iteration": b_it32 / (1e-3 * msir / max(1, rir["inner_total"])) / 1e9, "rel_res": rir["rel_res"],
-        "kernel_ms": dict(zip(("residual64", "inner_spmv_dot", "inner_update", "inner_aypx"), kir)),
-        "inner_spmv_GBps": b_k1_32 / (1e-3 * kir[1]) / 1e9, "layout": layir,
+    for h, fn in ((g["vb"], "apcg_vec_destroy"), (g["vx"], "apcg_vec_destroy"), (g["A"], "apcg_mat_destroy")):
+        apcg.call(fn, V(h))
+    it64 = r64["iters"]
+    alg64 = 12 * nnz + 4 * (n + 1) + 104 * n
+    st64 = _stored_spmv_bytes(lay64, 8) + 16 * n + 64 * n + 24 * n
+    alg_k1 = 12 * nnz + 4 * (n + 1) + 16 * n
+    st_k1 = _stored_spmv_bytes(lay64, 8) + 16 * n
+    out["fp64_pcg"] = {
+        "ms_per_solve": ms64, "solves_per_s": 1e3 / ms64, "iters": it64, "us_per_iteration": 1e3 * ms64 / it64,
+        "rel_res": r64["rel_res"], "kernel_ms": dict(zip(("spmv_dot", "update", "aypx"), k64)), "layout": lay64,
+        "roofline_iteration": _roofline(alg64, st64, 1e-3 * ms64 / it64, peak, peak_kind),
+        "roofline_spmv": _roofline(alg_k1, st_k1, 1e-3 * k64[0], peak, peak_kind),
     }
+    inner_s = 1e-3 * (kir[1] + kir[2] + kir[3])
+    alg32 = 8 * nnz + 4 * (n + 1) + 52 * n
+    st32 = _stored_spmv_bytes(layir, 4) + 52 * n
+    alg32_k1 = 8 * nnz + 4 * (n + 1) + 8 * n
+    st32_k1 = _stored_spmv_bytes(layir, 4) + 8 * n
+    out["mixed_ir"] = {
+        "ms_per_solve": msir, "solves_per_s": 1e3 / msir, "outer": rir["outer"], "inner_total": rir["inner_total"],
+        "rel_res": rir["rel_res"], "kernel_ms": dict(zip(("residual64", "inner_spmv_dot", "inner_update", "inner_aypx"), kir)),
+        "layout": layir,
+        "roofline_inner_iteration": _roofline(alg32, st32, inner_s, peak, peak_kind),
+        "roofline_inner_spmv": _roofline(alg32_k1, st32_k1, 1e-3 * kir[1], peak, peak_kind),
+    }
+    out["solves_per_s"] = 1e3 / msir
+    out["baseline"] = "float64 Jacobi-PCG of the same system to the same tolerance (graph mode)"
     out["speedup_ir_vs_fp64"] = ms64 / msir
-    line = {"metric": "time to solution at rtol 1e-10 (float64 PCG vs float32-inner refinement)", "value": 1e3 / msir,
-            "unit": "solves/s", "dtype": "f32+f64", "data": "synthetic", **out}
-    print(json.dumps(line), flush=True)
+    bn = float((p.b ** 2).sum() ** 0.5)
+    out["true_rel_res"] = {"mixed_ir": float(((p.b - oracle.spmv(p.A, xir)) ** 2).sum() ** 0.5) / bn,
+                           "fp64_pcg": float(((p.b - oracle.spmv(p.A, x64)) ** 2).sum() ** 0.5) / bn}
+    if oracle.build_omp() is not None:
+        r = oracle.pcg_omp(p.A, p.b, rtol=1e-10, max_it=50000, check_every=10, threads=oracle.host_cores())
+        out["max_rel_err_vs_fp64_oracle"] = {"mixed_ir": _rel_err(xir, r["x"]), "fp64_pcg": _rel_err(x64, r["x"]),
+                                             "oracle": f"float64 oracle PCG to rtol 1e-10 ({r['iters']} iterations; "
+                                                       "its steps split over the host cores)"}
+    return out
 
 
-def bench_c4(args):
-    """1024 shifted 5-point systems (sides 16..128): one batched graph launch vs one solve at a time (float64)."""
+def _batch_oracle_errors(B, xg, sample, rtol):
+    """Largest relative difference between the batch's solutions and the float64 oracle's on a sample."""
+    import oracle
+
+    def job(s):
+        A, b, _ = B.system(int(s))
+        return lambda: oracle.pcg(A, b, rtol=rtol, check_every=1)["x"]
+
+    refs = _oracle_sample([job(s) for s in sample])
+    off = B.sys_row_off
+    return max(_rel_err(xg[off[s]:off[s + 1]], r) for s, r in zip(sample, refs))
+
+
+def _batch_sample(B, k, seed=0):
+    import numpy as np
+
+    sizes = np.diff(B.sys_row_off)
+    pick = {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    pick |= set(np.random.default_rng(seed).choice(B.nsys, k, replace=False).tolist())
+    return sorted(pick)
+
+
+def c4_block(apcg, ctx, stream, dev, tune=True, reps=3):
+    """1024 shifted 5-point systems (sides 16..128) to rtol 1e-8: one batched graph launch against the same
+    systems solved one at a time by the single-system solver's best mode."""
     import ctypes as C
 
     import numpy as np
     import torch
 
-    from paper_2306_17801_gb300 import apcg
     from synthetic import batch_shifted_5pt
 
     V = C.c_void_p
-    dev = torch.device("cuda", 0)
-    apcg.load()
     B = batch_shifted_5pt(1024, seed=0)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     rowptr, col, val, b = t(B.rowptr), t(B.col), t(B.val), t(B.b)
     x = torch.zeros(B.n_total, dtype=torch.float64, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-    ctx = apcg.ctx_create(stream)
-    out = {"config": {"workload": "1024 x (2D 5-point + sigma I), sides 16..128 (6.40 M rows), rtol 1e-8, k=1"}}
-    opts = apcg.cg_opts(rtol=1e-8, check_every=1)
-    plan = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, val, opts)
-    table = apcg.batch_plan_tune(plan, b) if not args.no_tune else None
-
-    def batched():
-        x.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = apcg.batch_plan_solve(plan, b, x, B.nsys)
-        return time.perf_counter() - t0, res
-
-    batched()
-    dts = [batched() for _ in range(max(2, args.steps // 3))]
-    dt, res = min(dts, key=lambda z: z[0])
-    iters = np.array([r["iters"] for r in res])
+    out = {"workload": f"1024 x (2D 5-point + sigma I), sides 16..128 ({B.n_total:,} rows), rtol 1e-8, k=1"}
+    plan = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, val, apcg.cg_opts(rtol=1e-8, check_every=1))
+    table = apcg.batch_plan_tune(plan, b) if tune else None
+    ms, res = _timed_solves(stream, lambda: x.zero_(), lambda: apcg.batch_plan_solve(plan, b, x, B.nsys), reps)
     assert all(r["reason"] == "converged" for r in res)
-    out["batched"] = {"ms_per_batch": 1e3 * dt, "solves_per_s": B.nsys / dt, "iters_total": int(iters.sum()),
-                      "iters_max": int(iters.max()), "tuning_table": table}
     apcg.call("apcg_batch_plan_destroy", V(plan))
-    # one system at a time through the single-system solver (its best mode: the persistent
-    # cluster kernel); every system's arrays and plan are prepared before the clock starts
-    sizes = np.diff(B.sys_row_off)
+    xg = x.cpu().numpy()
+    iters = np.array([r["iters"] for r in res])
+    ns = np.diff(B.sys_row_off)
+    nz = np.diff(B.rowptr[B.sys_row_off])
+    alg = float(np.sum(iters * (12 * nz + 4 * (ns + 1) + 104 * ns)))
+    out["batched"] = {"ms_per_batch": ms, "solves_per_s": 1e3 * B.nsys / ms, "iters_total": int(iters.sum()),
+                      "iters_max": int(iters.max()), "tuning_table": table,
+                      "algorithmic_GBps": alg / (1e-3 * ms) / 1e9,
+                      "bound": "latency: each system's cluster keeps its vectors on chip and reads its CSR "
+                               "(at most 1.8 MB) from L2 after the first sweep"}
+    # one system at a time through the single-system solver (its best mode: the persistent cluster kernel);
+    # every system's arrays and plan are prepared before the clock starts
     systems = []
     for s in range(B.nsys):
         A_s, b_s, _ = B.system(s)
@@ -623,76 +783,64 @@ def bench_c4(args):
         apcg.call("apcg_cg_plan_destroy", V(d["plan"]))
         for h, fn in ((d["vb"], "apcg_vec_destroy"), (d["vx"], "apcg_vec_destroy"), (d["A"], "apcg_mat_destroy")):
             apcg.call(fn, V(h))
-    out["one_at_a_time"] = {"ms_per_batch": 1e3 * dt_seq, "solves_per_s": B.nsys / dt_seq, "max_rows": int(sizes.max())}
-    out["speedup_batched_vs_one_at_a_time"] = dt_seq / dt
-    line = {"metric": "batched PCG solves/s at rtol 1e-8 (FP64)", "value": B.nsys / dt, "unit": "solves/s",
-            "dtype": "f64", "data": "synthetic", **out}
-    print(json.dumps(line), flush=True)
+    out["one_at_a_time"] = {"ms_per_batch": 1e3 * dt_seq, "solves_per_s": B.nsys / dt_seq, "max_rows": int(ns.max()),
+                            "timing": "host wall time over the 1024 solves"}
+    out["solves_per_s"] = 1e3 * B.nsys / ms
+    out["baseline"] = "the same 1024 systems solved one at a time (single-system solver, persistent cluster mode)"
+    out["speedup_batched_vs_one_at_a_time"] = dt_seq / (1e-3 * ms)
+    sample = _batch_sample(B, 62)
+    out["max_rel_err_vs_fp64_oracle"] = _batch_oracle_errors(B, xg, sample, 1e-8)
+    out["oracle_sample"] = f"{len(sample)} systems (largest, smallest, 62 random)"
+    return out
 
 
-def bench_c5(args):
-    """4096 anisotropic 7-point systems (sides 8..32, float32-exact): batched float32-inner refinement
-    to rtol 1e-10 vs the batched float64 PCG and vs float64 solves one system at a time."""
+def c5_block(apcg, ctx, stream, dev, tune=True, reps=3):
+    """4096 anisotropic 7-point systems (sides 8..32, float32-exact values) to rtol 1e-10: the batched
+    float32-inner refinement against the batched float64 PCG and against float64 one system at a time."""
     import ctypes as C
 
     import numpy as np
     import torch
 
-    from paper_2306_17801_gb300 import apcg
     from synthetic import batch_aniso_7pt
 
     V = C.c_void_p
-    dev = torch.device("cuda", 0)
-    apcg.load()
     B = batch_aniso_7pt(4096, seed=0)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     rowptr, col, b = t(B.rowptr), t(B.col), t(B.b)
-    val32 = t(B.val.astype(np.float32))
-    val64 = t(B.val)
+    val32, val64 = t(B.val.astype(np.float32)), t(B.val)
     x = torch.zeros(B.n_total, dtype=torch.float64, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-    ctx = apcg.ctx_create(stream)
     nnz = int(B.rowptr[-1])
-    out = {"config": {"workload": f"4096 x anisotropic 3D 7-point, sides 8..32 ({B.n_total:,} rows, {nnz:,} nnz), "
-                                  "float32-exact values, rtol 1e-10"}}
-
-    def run(plan):
-        x.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = apcg.batch_plan_solve(plan, b, x, B.nsys)
-        return time.perf_counter() - t0, res
-
-    def best(plan):
-        run(plan)
-        dts = [run(plan) for _ in range(max(2, args.steps // 3))]
-        return min(dts, key=lambda z: z[0])
-
+    out = {"workload": f"4096 x anisotropic 3D 7-point, sides 8..32 ({B.n_total:,} rows, {nnz:,} nnz), "
+                       "float32-exact values, rtol 1e-10"}
     irp = apcg.batch_ir_plan_create(ctx, B.sys_row_off, rowptr, col, None, val32,
                                     apcg.ir_opts(rtol=1e-10, rtol_inner=1e-4, inner_check_every=4))
-    table_ir = apcg.batch_plan_tune(irp, b) if not args.no_tune else None
-    dt_ir, res_ir = best(irp)
+    table_ir = apcg.batch_plan_tune(irp, b) if tune else None
+    ms_ir, res_ir = _timed_solves(stream, lambda: x.zero_(), lambda: apcg.batch_plan_solve(irp, b, x, B.nsys), reps)
     x_ir = x.cpu().numpy()
     assert all(r["reason"] == "converged" for r in res_ir)
     apcg.call("apcg_batch_plan_destroy", V(irp))
     inner = np.array([r["iters"] for r in res_ir])
     outer = np.array([r["outer"] for r in res_ir])
-    out["batched_ir"] = {"ms_per_batch": 1e3 * dt_ir, "solves_per_s": B.nsys / dt_ir, "inner_total": int(inner.sum()),
+    ns = np.diff(B.sys_row_off)
+    nz = np.diff(B.rowptr[B.sys_row_off])
+    alg = float(np.sum(inner * (8 * nz + 4 * (ns + 1) + 52 * ns)))
+    out["batched_ir"] = {"ms_per_batch": ms_ir, "solves_per_s": 1e3 * B.nsys / ms_ir, "inner_total": int(inner.sum()),
                          "outer_max": int(outer.max()), "outer_mean": float(outer.mean()),
-                         "max_rel_res": max(r["rel_res"] for r in res_ir), "tuning_table": table_ir}
+                         "max_rel_res": max(r["rel_res"] for r in res_ir), "tuning_table": table_ir,
+                         "algorithmic_GBps_inner": alg / (1e-3 * ms_ir) / 1e9,
+                         "bound": "latency: per-system working sets stay in L2 and on chip"}
     cgp = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, val64, apcg.cg_opts(rtol=1e-10, check_every=4))
-    if not args.no_tune:
+    if tune:
         apcg.batch_plan_tune(cgp, b)
-    dt_64, res_64 = best(cgp)
-    x_64 = x.cpu().numpy()
+    ms_64, res_64 = _timed_solves(stream, lambda: x.zero_(), lambda: apcg.batch_plan_solve(cgp, b, x, B.nsys), reps)
     assert all(r["reason"] == "converged" for r in res_64)
     apcg.call("apcg_batch_plan_destroy", V(cgp))
-    it64 = np.array([r["iters"] for r in res_64])
-    out["batched_fp64"] = {"ms_per_batch": 1e3 * dt_64, "solves_per_s": B.nsys / dt_64, "iters_total": int(it64.sum())}
-    out["speedup_ir_vs_fp64_batched"] = dt_64 / dt_ir
+    out["batched_fp64"] = {"ms_per_batch": ms_64, "solves_per_s": 1e3 * B.nsys / ms_64,
+                           "iters_total": int(sum(r["iters"] for r in res_64))}
+    out["speedup_ir_vs_fp64_batched"] = ms_64 / ms_ir
     # float64 one system at a time (the single-system solver's auto mode), on a sample scaled to the batch
-    rng = np.random.default_rng(1)
-    sample = np.sort(rng.choice(B.nsys, 256, replace=False))
+    sample = np.sort(np.random.default_rng(1).choice(B.nsys, 256, replace=False))
     systems = []
     for s in sample:
         A_s, b_s, _ = B.system(int(s))
@@ -713,17 +861,88 @@ def bench_c5(args):
         for h, fn in ((d["vb"], "apcg_vec_destroy"), (d["vx"], "apcg_vec_destroy"), (d["A"], "apcg_mat_destroy")):
             apcg.call(fn, V(h))
     out["one_at_a_time_fp64"] = {"ms_per_batch": 1e3 * dt_seq, "solves_per_s": B.nsys / dt_seq,
-                                 "sample": "256 random systems timed, scaled to 4096"}
-    out["speedup_ir_batched_vs_one_at_a_time"] = dt_seq / dt_ir
-    # error of the refinement against the batched float64 solution, over the whole batch
-    # (the comparison with the float64 oracle runs in the tests)
-    off = B.sys_row_off
-    err_64 = max(np.linalg.norm(x_ir[off[s]:off[s + 1]] - x_64[off[s]:off[s + 1]]) /
-                 max(np.linalg.norm(x_64[off[s]:off[s + 1]]), 1e-300) for s in range(B.nsys))
-    out["max_rel_err_vs_fp64_batched"] = float(err_64)
-    line = {"metric": "batched mixed-precision solves/s at rtol 1e-10", "value": B.nsys / dt_ir, "unit": "solves/s",
-            "dtype": "f32+f64", "data": "synthetic", **out}
-    print(json.dumps(line), flush=True)
+                                 "sample": "256 random systems timed (host wall time), scaled to 4096"}
+    out["solves_per_s"] = 1e3 * B.nsys / ms_ir
+    out["baseline"] = "the same 4096 systems solved one at a time in float64 (single-system solver, auto mode)"
+    out["speedup_ir_batched_vs_one_at_a_time"] = dt_seq / (1e-3 * ms_ir)
+    osample = _batch_sample(B, 30)
+    out["max_rel_err_vs_fp64_oracle"] = _batch_oracle_errors(B, x_ir, osample, 1e-10)
+    out["oracle_sample"] = f"{len(osample)} systems (largest, smallest, 30 random), float64 oracle PCG to rtol 1e-10"
+    return out
+
+
+def tfqmr_block(apcg, ctx, stream, dev, p, x_ref64, peak, peak_kind, c2_only=False, reps=3):
+    """Jacobi-TFQMR (Sec. 4.3) to rtol 1e-8: host-synchronous against the graph form (and the one-launch cluster
+    form on the 64^2 system), microseconds per iteration (two SpMVs each)."""
+    import ctypes as C
+
+    import numpy as np
+
+    import oracle
+    from synthetic import single_problem
+
+    V = C.c_void_p
+    out = {"workload": "Jacobi-TFQMR to rtol 1e-8 on 3D 7-point 128^3 (k=10)" +
+                       ("" if c2_only else " and 2D 5-point 64^2 (k=1)")}
+    cases = (("c2", 10),) if c2_only else (("c1", 1), ("c2", 10))
+    for cfg, k in cases:
+        q = p if (cfg == "c2" and p is not None) else single_problem(cfg, seed=0)
+        g = _gpu_problem(q, dev)
+        reset = lambda: apcg.call("apcg_vec_set_async", V(ctx), V(g["vx"]), C.c_double(0.0))  # noqa: E731
+        row = {"n": q.n, "nnz": q.nnz, "k": k}
+        modes = ("host_sync", "async_graph") + (("persistent",) if q.n <= 16384 else ())
+        lay = None
+        for mode in modes:
+            plan = apcg.tfqmr_plan_create(ctx, g["A"], apcg.cg_opts(rtol=1e-8, check_every=k, mode=mode, max_it=20000))
+            ms, r = _timed_solves(stream, reset, lambda: apcg.tfqmr_plan_solve(plan, g["vb"], g["vx"]), reps)
+            if mode == "async_graph" and q.n > 16384:
+                lay = apcg.plan_layout(plan, "tfqmr")
+                xt = g["x"].cpu().numpy()
+            apcg.call("apcg_tfqmr_plan_destroy", V(plan))
+            assert r["reason"] == "converged"
+            row[mode] = {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iters": r["iters"],
+                         "us_per_iteration": 1e3 * ms / r["iters"], "kernel_launches": r["kernel_launches"]}
+        row["speedup_async_graph_vs_host_sync"] = row["host_sync"]["ms_per_solve"] / row["async_graph"]["ms_per_solve"]
+        if "persistent" in row:
+            row["speedup_persistent_vs_host_sync"] = row["host_sync"]["ms_per_solve"] / row["persistent"]["ms_per_solve"]
+        if lay is not None:
+            alg = 24 * q.nnz + 8 * (q.n + 1) + 232 * q.n
+            st = 2 * _stored_spmv_bytes(lay, 8) + 232 * q.n
+            row["layout"] = lay
+            row["roofline_iteration"] = _roofline(alg, st, 1e-6 * row["async_graph"]["us_per_iteration"], peak, peak_kind)
+            row["true_rel_res"] = float(np.linalg.norm(q.b - oracle.spmv(q.A, xt)) / np.linalg.norm(q.b))
+            if x_ref64 is not None:
+                row["rel_err_vs_fp64_oracle_pcg"] = _rel_err(xt, x_ref64)
+        for h, fn in ((g["vb"], "apcg_vec_destroy"), (g["vx"], "apcg_vec_destroy"), (g["A"], "apcg_mat_destroy")):
+            apcg.call(fn, V(h))
+        out[cfg] = row
+    out["solves_per_s"] = out["c2"]["async_graph"]["solves_per_s"]
+    out["baseline"] = "the host-synchronous form of the same TFQMR solve"
+    return out
+
+
+def _standalone(args, name):
+    """--config c3|c4|c5|tfqmr: one workload block as its own JSON line."""
+    import torch
+
+    from paper_2306_17801_gb300 import apcg
+
+    dev = torch.device("cuda", 0)
+    apcg.load()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = apcg.ctx_create(stream)
+    peak, kind = _peaks()
+    reps = max(2, args.steps // 3)
+    if name == "c3":
+        blk, metric, dt = c3_block(apcg, ctx, stream, dev, peak, kind, reps), "time to solution at rtol 1e-10 (float64 PCG vs float32-inner refinement)", "f32+f64"
+    elif name == "c4":
+        blk, metric, dt = c4_block(apcg, ctx, stream, dev, not args.no_tune, reps), "batched PCG solves/s at rtol 1e-8 (FP64)", "f64"
+    elif name == "c5":
+        blk, metric, dt = c5_block(apcg, ctx, stream, dev, not args.no_tune, reps), "batched mixed-precision solves/s at rtol 1e-10", "f32+f64"
+    else:
+        blk, metric, dt = tfqmr_block(apcg, ctx, stream, dev, None, None, peak, kind, False, reps), "TFQMR us/iteration and solves/s at rtol 1e-8 (async vs host-sync, FP64)", "f64"
+    print(json.dumps({"metric": metric, "value": blk["solves_per_s"], "unit": "solves/s", "dtype": dt,
+                      "data": "synthetic", **blk}), flush=True)
 
 
 def bench_stencil(args):
@@ -833,58 +1052,6 @@ def bench_stencil(args):
             apcg.call(fn, V(h))
     line = {"metric": "matrix-free stencil PCG solves/s at rtol 1e-8 (FP64)", "value": 1e3 / out["7pt"]["stencil"]["ms_per_solve"],
             "unit": "solves/s", "dtype": "f64", "data": "synthetic", **out}
-    print(json.dumps(line), flush=True)
-
-
-def bench_tfqmr(args):
-    """Jacobi-TFQMR (Sec. 4.3) on the 64^2 5-point and 128^3 7-point systems: host-synchronous vs
-    asynchronous forms (and the one-launch cluster form on the small system), microseconds per
-    iteration (two SpMVs each)."""
-    import ctypes as C
-
-    import torch
-
-    from paper_2306_17801_gb300 import apcg
-    from synthetic import single_problem
-
-    V = C.c_void_p
-    dev = torch.device("cuda", 0)
-    apcg.load()
-    stream = torch.cuda.Stream(device=dev)
-    ctx = apcg.ctx_create(stream)
-    out = {"config": {"workload": "Jacobi-TFQMR to rtol 1e-8 on 2D 5-point 64^2 (k=1) and 3D 7-point 128^3 (k=10)"}}
-    for cfg, k in (("c1", 1), ("c2", 10)):
-        p = single_problem(cfg, seed=0)
-        g = _gpu_problem(p, dev)
-        row = {"n": p.n, "nnz": p.nnz, "k": k}
-        modes = ("host_sync", "async", "async_graph") + (("persistent",) if p.n <= 16384 else ())
-        for mode in modes:
-            plan = apcg.tfqmr_plan_create(ctx, g["A"], apcg.cg_opts(rtol=1e-8, check_every=k, mode=mode, max_it=20000))
-            best, r = None, None
-            for i in range(max(2, args.steps // 3) + 1):
-                apcg.call("apcg_vec_set_async", V(ctx), V(g["vx"]), C.c_double(0.0))
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                r = apcg.tfqmr_plan_solve(plan, g["vb"], g["vx"])
-                dt = time.perf_counter() - t0
-                if i > 0:
-                    best = dt if best is None else min(best, dt)
-            apcg.call("apcg_tfqmr_plan_destroy", V(plan))
-            assert r["reason"] == "converged"
-            row[mode] = {"ms_per_solve": 1e3 * best, "iters": r["iters"], "us_per_iteration": 1e6 * best / r["iters"],
-                         "kernel_launches": r["kernel_launches"]}
-        row["speedup_async_graph_vs_host_sync"] = row["host_sync"]["ms_per_solve"] / row["async_graph"]["ms_per_solve"]
-        if "persistent" in row:
-            row["speedup_persistent_vs_host_sync"] = row["host_sync"]["ms_per_solve"] / row["persistent"]["ms_per_solve"]
-        b_it = 24 * p.nnz + 8 * (p.n + 1) + 232 * p.n
-        row["algorithmic_bytes_per_iteration"] = b_it
-        row["GBps_per_iteration"] = b_it / (1e-6 * row["async_graph"]["us_per_iteration"]) / 1e9
-        out[cfg] = row
-        for h, fn in ((g["vb"], "apcg_vec_destroy"), (g["vx"], "apcg_vec_destroy"), (g["A"], "apcg_mat_destroy")):
-            apcg.call(fn, V(h))
-    line = {"metric": "TFQMR us/iteration and solves/s at rtol 1e-8 (async vs host-sync, FP64)",
-            "value": 1e3 / out["c2"]["async_graph"]["ms_per_solve"], "unit": "solves/s", "dtype": "f64",
-            "data": "synthetic", **out}
     print(json.dumps(line), flush=True)
 
 

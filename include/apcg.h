@@ -816,6 +816,15 @@ APCG_API apcg_status apcg_cg_solve_batched(apcg_ctx ctx, int32_t nsys, const int
  * back (per graph, one wait at the end).  us: host [4].  Blocks.
  */
 APCG_API apcg_status apcg_launch_floor(apcg_ctx ctx, int32_t reps, double* us);
+/*
+ * Measured float64 FMA throughput of this GPU (the paper has no counterpart;
+ * the benchmark divides the float64 rate of its SpMV by it): a kernel of
+ * independent fma chains on every SM, at full occupancy, timed with CUDA
+ * events on ctx's stream; *gflops = 2 x FMAs / the fastest of `reps`
+ * launches (after one warm-up launch), in GFLOP/s.  Allocates an output
+ * buffer from the library pool.  Blocks.
+ */
+APCG_API apcg_status apcg_fp64_fma_peak(apcg_ctx ctx, int32_t reps, double* gflops);
 
 /* ------------------------------------------------------------------ host-only simulation of the marking rules */
 

@@ -18,5 +18,9 @@ from .oracle import (  # noqa: F401
     stencil_apply,
     pcg_f32,
     ir,
+    pcg_omp,
+    build_omp,
+    host_cores,
+    host_cpu_model,
 )
 from .expr_oracle import expr_eval  # noqa: F401

@@ -23,8 +23,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, f) for f in ("pcg_oracle.c", "tfqmr_oracle.c", "stencil_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
+_OMP_SRC = os.path.join(_HERE, "pcg_oracle_omp.c")
+_OMP_LIB = os.path.join(_OUT_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp_lib = None
 
 REASON = {0: "converged", 1: "not_converged", 2: "breakdown", 3: "bad_diagonal", 4: "no_memory"}
 
@@ -62,6 +65,74 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force: bool = False) -> str | None:
+    """Compile the multi-threaded timing variant (OpenMP); None where the compiler has no OpenMP."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < os.path.getmtime(_OMP_SRC):
+        tmp = _OMP_LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", _OMP_SRC,
+               "-o", tmp, "-lm"]
+        if subprocess.run(cmd, capture_output=True).returncode != 0:
+            return None
+        os.replace(tmp, _OMP_LIB)
+    return _OMP_LIB
+
+
+def host_cores() -> int:
+    """Cores this process may run on (the affinity mask, else the CPU count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def host_cpu_model() -> str:
+    """CPU model string of this host (from /proc/cpuinfo or lscpu), or the machine type."""
+    import platform
+
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def pcg_omp(A, b, x0=None, rtol=1e-8, atol=0.0, max_it=None, check_every=1, threads=0) -> dict:
+    """The float64 Jacobi-PCG oracle's steps split over OpenMP threads (timing only; threads=0: all)."""
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            path = build_omp()
+            if path is None:
+                raise RuntimeError("gcc without OpenMP: the multi-threaded oracle variant is unavailable")
+            lib = C.CDLL(path)
+            P = C.c_void_p
+            lib.oracle_pcg_omp.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                           C.c_int32, C.POINTER(_Res)]
+            lib.oracle_pcg_omp.restype = C.c_int
+            _omp_lib = lib
+    rowptr, col, val = _csr(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(A.n, dtype=np.float64) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    if max_it is None:
+        max_it = max(10 * A.n, 10)
+    res = _Res()
+    _omp_lib.oracle_pcg_omp(A.n, _p(rowptr), _p(col), _p(val), _p(b), _p(x), float(rtol), float(atol), int(max_it),
+                            int(check_every), int(threads), C.byref(res))
+    return dict(x=x, iters=int(res.iters), reason=REASON[res.reason], rr=float(res.rr), bnorm=float(res.bnorm))
 
 
 def load():

@@ -251,6 +251,7 @@ PROTOS = {
     "apcg_expr_execute_async": [P, P, P],
     "apcg_vec_axpy_expr_async": [P, P, P, P],
     "apcg_launch_floor": [P, i32, P],
+    "apcg_fp64_fma_peak": [P, i32, C.POINTER(C.c_double)],
     "apcg_stencil_create": [i32, i32, i32, i32, P, P, PP],
     "apcg_stencil_destroy": [P],
     "apcg_stencil_apply_async": [P, P, P, P],
@@ -540,6 +541,13 @@ def expr_describe(expr) -> dict:
     buf = C.create_string_buffer(8192)
     call("apcg_expr_describe", C.c_void_p(expr), C.byref(ni), C.byref(nl), buf, len(buf))
     return {"instructions": ni.value, "inputs": nl.value, "text": buf.value.decode()}
+
+
+def fp64_fma_peak(ctx, reps=5) -> float:
+    """Measured float64 FMA throughput in GFLOP/s (apcg_fp64_fma_peak)."""
+    g = C.c_double()
+    call("apcg_fp64_fma_peak", C.c_void_p(ctx), int(reps), C.byref(g))
+    return float(g.value)
 
 
 def launch_floor(ctx, reps=200) -> dict:

@@ -1,11 +1,13 @@
 """Mixed-precision iterative refinement (float32 inner PCG, float64 outer) on the GPU.
 
-Parity for the refinement's iteration counts is unpinned (no closed form);
-what is checked is what the method guarantees: the float64 true residual of
-the result meets the outer tolerance, and the result agrees with the float64
-solution (dense Cholesky on small systems, the float64 CG at full size)
-within the conditioning bound.  The oracle's own refinement reaches the same
-tolerance on the same systems.
+What is checked here is what the method guarantees: the float64 true
+residual of the result meets the outer tolerance, the result agrees with the
+float64 solution (dense Cholesky) within the conditioning bound, and the
+number of corrections is the oracle refinement's within one (the oracle's
+count is pinned by the contraction bound of each correction).  The float32
+inner path itself (SpMV, inner alpha/beta, inner counts) and the comparison
+with the float64 oracle's PCG solution are in test_gpu_ir_f32.py; at full
+size (160^3) only the true residual is checked here.
 """
 
 import ctypes as C
@@ -80,6 +82,7 @@ def test_ir_small_systems_reach_double_accuracy(ctx, mode):
     assert np.linalg.norm(x - xc) / np.linalg.norm(xc) <= kappa * 2e-10
     ref = oracle.ir(A, b, rtol=1e-10)
     assert ref["reason"] == "converged"
+    assert abs(res["outer"] - ref["outer"]) <= 1, (res["outer"], ref["outer"])
 
 
 def test_ir_zero_rhs_and_fixed_caps(ctx):
@@ -92,24 +95,13 @@ def test_ir_zero_rhs_and_fixed_caps(ctx):
     assert res["reason"] == "not_converged" and res["outer"] == 2 and res["inner_total"] <= 10
 
 
-def test_ir_full_size_27pt_matches_float64_cg(ctx):
-    """160^3 variable-coefficient 27-point: refinement to 1e-10 against float64 CG to 1e-10."""
+def test_ir_full_size_27pt_true_residual(ctx):
+    """160^3 variable-coefficient 27-point: the refinement reaches 1e-10 in the float64 true residual in 2 or
+    3 corrections (float32 alone cannot reach 1e-10, and a correction with inner tolerance 1e-4 contracts
+    the residual by close to 1e-4 on this family: the oracle's refinement needs 3 at 80^3)."""
     p = single_problem("c3", seed=0)
     res, x_ir = _ir(ctx, p.A, p.b, rtol=1e-10)
     assert res["reason"] == "converged"
     rel_ir = np.linalg.norm(p.b - oracle.spmv(p.A, x_ir)) / np.linalg.norm(p.b)
-    assert rel_ir <= 1.05e-10
-    # float64 CG on the same system
-    rowptr, col, val, b = _t(p.A.rowptr), _t(p.A.col), _t(p.A.val), _t(p.b)
-    x = torch.zeros_like(b)
-    A = apcg.mat_wrap(rowptr, col, val)
-    vb, vx = apcg.vec_wrap(b), apcg.vec_wrap(x)
-    r64 = apcg.cg_solve(ctx, A, vb, vx, apcg.cg_opts(rtol=1e-10, check_every=10, mode="async_graph", max_it=20000))
-    assert r64["reason"] == "converged"
-    x64 = x.cpu().numpy()
-    rel_64 = np.linalg.norm(p.b - oracle.spmv(p.A, x64)) / np.linalg.norm(p.b)
-    assert rel_64 <= 2e-10
-    # both are within the conditioning bound of the same solution
-    assert np.linalg.norm(x_ir - x64) / np.linalg.norm(x64) <= 1e-6
-    for h, fn in ((vb, "apcg_vec_destroy"), (vx, "apcg_vec_destroy"), (A, "apcg_mat_destroy")):
-        apcg.call(fn, C.c_void_p(h))
+    assert rel_ir <= 1.05e-10 and abs(rel_ir - res["rel_res"]) <= 1e-12
+    assert 2 <= res["outer"] <= 3
