@@ -93,6 +93,28 @@ Args<T> make_args(const CgCore<T>& c, T* x) {
 
 __device__ __forceinline__ int32_t read_done(const CgState* st) { return *(volatile const int32_t*)&st->done; }
 
+// The state block copied into shared memory at kernel entry by asynchronous 16-byte copies (cp.async, one
+// per thread of the first warp; the threads do not wait for them), so that the block completing a grid
+// reduction reads the scalars of its epilogue without a round trip to L2 in its serial tail.  The copy is
+// taken at entry; only that last block writes the state during the kernel.
+constexpr int kStateChunks = (int)(sizeof(CgState) / 16);
+static_assert(sizeof(CgState) % 16 == 0, "state block copied in 16-byte pieces");
+
+__device__ __forceinline__ void state_prefetch(const CgState* st, CgState* s) {
+  if (threadIdx.x < kStateChunks) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char*>(s) + 16 * threadIdx.x);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                 "l"(__cvta_generic_to_global(reinterpret_cast<const char*>(st) + 16 * threadIdx.x))
+                 : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+}
+
+// Completes the copy; the barriers of the grid reduction that follows make it visible to the whole block.
+__device__ __forceinline__ void state_prefetch_wait() {
+  if (threadIdx.x < kStateChunks) asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // r = b - A x0, z = D^-1 r, p = z; rho = (r,z), rr = (r,r), bb = (b,b) (float64 solve).
 // spmv(epi) applies the operator to x with the given row epilogue.
 template <class Spmv>
@@ -147,18 +169,19 @@ __global__ void __launch_bounds__(kThreads) setup_stencil_kernel(Args<double> a,
              [&](auto epi) { dev::stencil_spmv<NP, false, double>(S, a.x, epi); });
 }
 
-// The last block of K1: gamma, and alpha = rho / gamma (device mode) or a breakdown flag.
+// The last block of K1: gamma, and alpha = rho / gamma (device mode) or a breakdown flag.  pre: the state
+// as the kernel found it (done was 0: the kernel returns at entry otherwise).
 template <bool HOST, class T>
-__device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma) {
+__device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma, const CgState& pre) {
   CgState* st = a.st;
   st->gamma = gamma;
-  if (!HOST && st->done == 0) {
+  if (!HOST) {
     if (!(gamma > T(0)) || !isfinite(gamma)) {
       st->done = kDoneBreakdown;
     } else {
-      const T alpha = (T)st->rho / gamma;
+      const T alpha = (T)pre.rho / gamma;
       st->alpha = alpha;
-      if (st->iter < st->hist_len) a.alpha_h[st->iter] = alpha;
+      if (pre.iter < pre.hist_len) a.alpha_h[pre.iter] = alpha;
     }
   }
 }
@@ -168,6 +191,8 @@ __device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma) {
 template <bool HOST, bool LONG, class T, int G = 8, int CF = dev::kColIndex, bool STAGED = false>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   if (!HOST && read_done(a.st)) return;
+  __shared__ __align__(16) CgState pre;
+  if (!HOST) state_prefetch(a.st, &pre);
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
   auto epi = [&](int32_t i, T s, T p_i) {
@@ -184,22 +209,26 @@ __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   } else {
     dev::sell_spmv<true, LONG, T, G, CF>(a.A, a.p, epi);
   }
+  if (!HOST) state_prefetch_wait();
   T tot[1];
-  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0]);
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0], pre);
 }
 
 // K1 on a stencil operator (stencil.cuh): the same per-row arithmetic.
 template <bool HOST, int NP, class T>
 __global__ void __launch_bounds__(kThreads) k1_stencil_kernel(Args<T> a, dev::StencilView S) {
   if (!HOST && read_done(a.st)) return;
+  __shared__ __align__(16) CgState pre;
+  if (!HOST) state_prefetch(a.st, &pre);
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
   dev::stencil_spmv<NP, true, T>(S, a.p, [&](int32_t i, T s, T p_i) {
     a.w[i] = s;
     v[0] = fma(p_i, s, v[0]);
   });
+  if (!HOST) state_prefetch_wait();
   T tot[1];
-  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0]);
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0], pre);
 }
 
 // K2.  The test runs when the iteration count is a multiple of k or reaches
@@ -217,6 +246,8 @@ __global__ void __launch_bounds__(kThreads, 4) k2_kernel(Args<T> a, double alpha
     }
     return;
   }
+  __shared__ __align__(16) CgState pre;
+  if (!HOST) state_prefetch(a.st, &pre);
   const T alpha = HOST ? (T)alpha_host : (T)a.st->alpha;
   bool check = true;
   if (!HOST) {
@@ -295,6 +326,7 @@ __global__ void __launch_bounds__(kThreads, 4) k2_kernel(Args<T> a, double alpha
       if (check) v[1] = fma(ri, ri, v[1]);
     }
   }
+  if (!HOST) state_prefetch_wait();
   T tot[2];
   if (dev::grid_sum_last<2>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
     CgState* st = a.st;
@@ -302,28 +334,28 @@ __global__ void __launch_bounds__(kThreads, 4) k2_kernel(Args<T> a, double alpha
     st->rho_new = rz;
     if (check) st->rr = rr;
     if (!HOST) {
-      const int32_t it = st->iter + 1;
+      const int32_t it = pre.iter + 1;
       st->iter = it;
       int32_t done = 0;
       // An exactly zero residual ends the solve at any iteration; between
       // tests (r, D^-1 r) = 0 stands for r = 0 (D^-1 is positive).
       if ((check && rr == T(0)) || rz == T(0))
         done = kDoneConverged;
-      else if (check && sqrt(rr) <= (T)st->tol)
+      else if (check && sqrt(rr) <= (T)pre.tol)
         done = kDoneConverged;
-      else if (it >= st->max_it)
+      else if (it >= pre.max_it)
         done = kDoneNotConverged;
       else if (!isfinite(rz) || (check && !isfinite(rr)))
         done = kDoneBreakdown;
       if (!done) {
-        const T beta = rz / (T)st->rho;
+        const T beta = rz / (T)pre.rho;
         st->beta = beta;
         st->rho = rz;
-        if (it - 1 < st->hist_len) a.beta_h[it - 1] = beta;
+        if (it - 1 < pre.hist_len) a.beta_h[it - 1] = beta;
       }
       st->done = done;
       if (use_cond) {
-        st->body_runs += 1;
+        st->body_runs = pre.body_runs + 1;
         cudaGraphSetConditional(cond, done ? 0u : 1u);
       }
     }
