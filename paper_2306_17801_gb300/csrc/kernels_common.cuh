@@ -95,24 +95,31 @@ __device__ __forceinline__ void neg128(uint64_t& h, uint64_t& l) {
   h = ~h + (l == 0ull ? 1ull : 0ull);
 }
 
+// 64-bit shifts with PTX semantics: a shift amount of 64 or more yields 0 (no undefined behaviour, no branch).
+__device__ __forceinline__ uint64_t shl64(uint64_t x, unsigned s) {
+  uint64_t r;
+  asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+}
+__device__ __forceinline__ uint64_t shr64(uint64_t x, unsigned s) {
+  uint64_t r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+}
+
 // v * 2^(1075 - E + kShift) truncated toward zero, as a 128-bit two's-complement number (E >= exp_field(v),
-// E < kNonFinite).
+// E < kNonFinite).  Branch-free: lanes holding values of different scales do not diverge.
 __device__ __forceinline__ void to_fixed(double v, unsigned E, uint64_t& h, uint64_t& l) {
   const uint64_t bits = (uint64_t)__double_as_longlong(v);
   const unsigned ef = (unsigned)(bits >> 52) & 0x7ffu;
-  uint64_t m = bits & ((1ull << 52) - 1ull);
-  if (ef) m |= 1ull << 52;
+  const uint64_t m = (bits & ((1ull << 52) - 1ull)) | (ef ? (1ull << 52) : 0ull);
   const int sh = (int)(ef ? ef : 1u) - (int)E + kShift;  // <= kShift < 64
-  if (sh > 0) {
-    h = m >> (64 - sh);
-    l = m << sh;
-  } else if (sh > -64) {
-    h = 0ull;
-    l = m >> (-sh);
-  } else {
-    h = l = 0ull;
-  }
-  if (bits >> 63) neg128(h, l);
+  h = shr64(m, (unsigned)(64 - sh));                      // 0 unless sh > 0
+  l = sh >= 0 ? shl64(m, (unsigned)sh) : shr64(m, (unsigned)(-sh));
+  const uint64_t nl = ~l + 1ull, nh = ~h + (l == 0ull ? 1ull : 0ull);
+  const bool neg = (bits >> 63) != 0ull;
+  l = neg ? nl : l;
+  h = neg ? nh : h;
 }
 
 // Bits [24j, 24j + 24) of the 128-bit pattern (h, l).
@@ -204,21 +211,28 @@ __device__ __forceinline__ void block_sum_fixed(const uint64_t (&h)[NV], const u
     uint64_t S = 0ull;  // lane t < 6 NV: limb t % 6 of value t / 6 summed over the warps (< 2^34)
     if (lane < 6 * NV)
       for (int w = 0; w < nw; ++w) S += s[lane * 32 + w];
+    // lane k < NV assembles value k from its six limb sums and rounds it
+    const int kk = lane < NV ? lane : 0;
+    uint64_t th = 0ull, tl = 0ull;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const uint64_t Sj = __shfl_sync(kFull, S, kk * 6 + j);
+      const int sh = 24 * j;
+      if (sh == 0)
+        add128(th, tl, 0ull, Sj);
+      else if (sh < 64)
+        add128(th, tl, Sj >> (64 - sh), Sj << sh);
+      else
+        add128(th, tl, Sj << (sh - 64), 0ull);
+    }
+    unsigned Ek = E[0];
+#pragma unroll
+    for (int k = 1; k < NV; ++k) Ek = kk == k ? E[k] : Ek;
+    const double r = Ek >= kNonFinite ? __longlong_as_double(0x7ff8000000000000ll) : from_fixed(th, tl, Ek);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      uint64_t th = 0ull, tl = 0ull;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const uint64_t Sj = __shfl_sync(kFull, S, k * 6 + j);
-        const int sh = 24 * j;
-        if (sh == 0)
-          add128(th, tl, 0ull, Sj);
-        else if (sh < 64)
-          add128(th, tl, Sj >> (64 - sh), Sj << sh);
-        else
-          add128(th, tl, Sj << (sh - 64), 0ull);
-      }
-      if (lane == 0) out[k] = E[k] >= kNonFinite ? __longlong_as_double(0x7ff8000000000000ll) : from_fixed(th, tl, E[k]);
+      const double rk = __shfl_sync(kFull, r, k);
+      if (lane == 0) out[k] = rk;
     }
   }
 }
@@ -244,28 +258,10 @@ __device__ __forceinline__ void block_sum_exact(double (&v)[NV], double* smem) {
   fx::block_sum_fixed<NV>(h, l, E, s + NV * 32, v);
 }
 
-// Deterministic grid-wide sum of NV float64 values per thread, exact up to one rounding per block and one at
-// the end (fx above): each block writes its exact block sums to partials[k * gridDim.x + blockIdx.x]; the
-// block that arrives last (atomic ticket) adds the partials exactly and returns true; only its thread 0
-// holds valid totals in tot[].  The ticket is reset to zero for the next kernel.  partials must hold
-// NV * gridDim.x values (gridDim.x <= 16 * blockDim.x) and smem NV * blockDim.x values.
+// The last block's exact sum of the float64 partials of a grid reduction (fx above): partials[k * gridDim.x
+// + i], gridDim.x <= 16 * blockDim.x; thread 0 receives the totals.  smem: NV * blockDim.x doubles.
 template <int NV>
-__device__ __forceinline__ bool grid_sum_last_exact(double (&v)[NV], double* partials, unsigned int* ticket,
-                                                    double* smem, double (&tot)[NV]) {
-  __shared__ bool s_last;
-  block_sum_exact<NV>(v, smem);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
-    // one acquire-release increment: its release orders this block's partials before it, its acquire
-    // (in the block that arrives last) orders every block's partials before the loads below, which the
-    // barrier then extends to the block's other threads
-    unsigned t;
-    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(ticket) : "memory");
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return false;
+__device__ __forceinline__ void grid_partials_exact(const double* partials, double* smem, double (&tot)[NV]) {
   // this thread's partials i = threadIdx.x + j * blockDim.x: the first kKeep kept in registers between the
   // pass that finds the largest exponent and the pass that converts them
   constexpr int kKeep = 4;
@@ -284,7 +280,6 @@ __device__ __forceinline__ bool grid_sum_last_exact(double (&v)[NV], double* par
     for (int i = (int)threadIdx.x + kKeep * bd; i < G; i += bd) E[k] = max(E[k], fx::exp_field(__ldcg(partials + k * G + i)));
   }
   unsigned* s = reinterpret_cast<unsigned*>(smem);
-  __syncthreads();
   fx::block_max<NV>(E, s);
   uint64_t h[NV], l[NV];
 #pragma unroll
@@ -304,44 +299,63 @@ __device__ __forceinline__ bool grid_sum_last_exact(double (&v)[NV], double* par
     }
   }
   fx::block_sum_fixed<NV>(h, l, E, s + NV * 32, tot);
-  if (threadIdx.x == 0) *ticket = 0u;
-  return true;
 }
 
 // Deterministic grid-wide sum of NV values per thread.  Each block writes its
 // NV block sums to partials[k * gridDim.x + blockIdx.x]; the block that
-// arrives last (atomic ticket) sums the partials in block order and returns
-// true; only its thread 0 holds valid totals in tot[].  The ticket is reset
-// to zero for the next kernel.  partials must hold NV * gridDim.x values and
-// smem NV * blockDim.x values.  float64 values take the exact integer path
-// above (grid_sum_last_exact); float32 values a float32 tree.
+// arrives last (one acquire-release ticket increment) sums the partials and
+// returns true; only its thread 0 holds valid totals in tot[].  The ticket is
+// reset to zero for the next kernel.  partials must hold NV * gridDim.x values
+// and smem NV * blockDim.x values.  float64 block sums take the exact integer
+// path above when kBlockExact; the last block's sum of the partials takes it
+// when kGridExact, and otherwise is a float64 tree in block order.  float32
+// values always take float32 trees.
+#ifndef APCG_BLOCK_EXACT
+#define APCG_BLOCK_EXACT 1
+#endif
+#ifndef APCG_GRID_EXACT
+#define APCG_GRID_EXACT 1
+#endif
+constexpr bool kBlockExact = APCG_BLOCK_EXACT != 0;
+constexpr bool kGridExact = APCG_GRID_EXACT != 0;
+
 template <int NV, class T>
 __device__ __forceinline__ bool grid_sum_last(T (&v)[NV], T* partials, unsigned int* ticket, T* smem, T (&tot)[NV]) {
-  if constexpr (std::is_same<T, double>::value) return grid_sum_last_exact<NV>(v, partials, ticket, smem, tot);
+  constexpr bool f64 = std::is_same<T, double>::value;
   __shared__ bool s_last;
-  block_sum<NV>(v, smem);
+  if constexpr (f64 && kBlockExact)
+    block_sum_exact<NV>(v, smem);
+  else
+    block_sum<NV>(v, smem);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
-    __threadfence();
-    const unsigned t = atomicAdd(ticket, 1u);
+    // one acquire-release increment: its release orders this block's partials before it, its acquire
+    // (in the block that arrives last) orders every block's partials before the loads below, which the
+    // barrier then extends to the block's other threads
+    unsigned t;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(ticket) : "memory");
     s_last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!s_last) return false;
-  __threadfence();
-  T s[NV];
+  if constexpr (f64 && kGridExact) {
+    grid_partials_exact<NV>(reinterpret_cast<const double*>(partials), reinterpret_cast<double*>(smem),
+                            reinterpret_cast<double(&)[NV]>(tot));
+  } else {
+    T s[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    s[k] = T(0);
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s[k] += __ldcg(partials + k * gridDim.x + i);
-  }
-  block_sum<NV>(s, smem);
-  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) {
+      s[k] = T(0);
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s[k] += __ldcg(partials + k * gridDim.x + i);
+    }
+    block_sum<NV>(s, smem);
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = s[k];
-    *ticket = 0u;
+      for (int k = 0; k < NV; ++k) tot[k] = s[k];
+    }
   }
+  if (threadIdx.x == 0) *ticket = 0u;
   return true;
 }
 
