@@ -398,6 +398,15 @@ def run_apcg(args, rank, world, local):
             "stored_bytes_per_iteration": stored_k1 + bytes_k2 + bytes_k3,
             "stored_frac_of_peak": (stored_k1 + bytes_k2 + bytes_k3) / (us_iter * 1e-6) / 1e9 / peak,
         }
+        # the iteration's other bound on GB300: float64 lane-operations (K1: one FMA per stored entry and per
+        # row; K2: four per row, five on test iterations; K3: one per row) at the measured float64 rate
+        fp64_ops = (lay["padded"] + n) + 4 * n + n / K_CHECK + n
+        out["iteration"]["fp64"] = {
+            "lane_ops_per_iteration": fp64_ops,
+            "floor_us": 2.0 * fp64_ops / (fp64_peak * 1e9) * 1e6,
+            "frac_of_floor": 2.0 * fp64_ops / (fp64_peak * 1e9) * 1e6 / us_iter,
+            "peak_gflops": fp64_peak,
+        }
         # ---- host-synchronous and launch-per-kernel forms of the same solve: minimum over repeated solves
         # (the paper's method, Sec. 4.1), CUDA events on the context stream
         modes = {}

@@ -123,7 +123,7 @@ apcg_status apcg_fp64_fma_peak(apcg_ctx ctx_in, int32_t reps, double* gflops) {
   int per_sm = 0;
   APCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma64_kernel, kFmaThreads, 0));
   const int grid = std::max(1, per_sm) * ctx_num_sms(ctx);
-  const int32_t iters = 4096;
+  const int32_t iters = 1024;
   double* sink = nullptr;
   APCG_TRY(dev_alloc_async((void**)&sink, sizeof(double) * (size_t)grid * kFmaThreads, s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
