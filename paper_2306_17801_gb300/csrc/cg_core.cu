@@ -170,12 +170,14 @@ __global__ void __launch_bounds__(kThreads) setup_stencil_kernel(Args<double> a,
 }
 
 // The last block of K1: gamma, and alpha = rho / gamma (device mode) or a breakdown flag.  pre: the state
-// as the kernel found it (done was 0: the kernel returns at entry otherwise).
-template <bool HOST, class T>
+// as the kernel found it (done was 0: the kernel returns at entry otherwise).  RECHECK: the kernel's own warps
+// may have set done meanwhile (a bounded wait of the staged SpMV that ran out); then gamma is incomplete and
+// done keeps that code.
+template <bool HOST, bool RECHECK, class T>
 __device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma, const CgState& pre) {
   CgState* st = a.st;
   st->gamma = gamma;
-  if (!HOST) {
+  if (!HOST && !(RECHECK && read_done(st))) {
     if (!(gamma > T(0)) || !isfinite(gamma)) {
       st->done = kDoneBreakdown;
     } else {
@@ -191,8 +193,10 @@ __device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma, const CgSta
 template <bool HOST, bool LONG, class T, int G = 8, int CF = dev::kColIndex, bool STAGED = false>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   if (!HOST && read_done(a.st)) return;
+  // the staged float32 instance keeps no copy: with it the compiler schedules the staged SpMV on 40 instead of
+  // 48 registers and the kernel runs about 40% slower (160^3 refinement, inner K1 100.6 -> 142.5 us)
   __shared__ __align__(16) CgState pre;
-  if (!HOST) state_prefetch(a.st, &pre);
+  if (!HOST && !STAGED) state_prefetch(a.st, &pre);
   __shared__ T red[kThreads];
   T v[1] = {T(0)};
   auto epi = [&](int32_t i, T s, T p_i) {
@@ -211,7 +215,8 @@ __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
   }
   if (!HOST) state_prefetch_wait();
   T tot[1];
-  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0], pre);
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0)
+    k1_finish<HOST, STAGED>(a, tot[0], STAGED ? *a.st : pre);
 }
 
 // K1 on a stencil operator (stencil.cuh): the same per-row arithmetic.
@@ -228,7 +233,8 @@ __global__ void __launch_bounds__(kThreads) k1_stencil_kernel(Args<T> a, dev::St
   });
   if (!HOST) state_prefetch_wait();
   T tot[1];
-  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) k1_finish<HOST>(a, tot[0], pre);
+  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0)
+    k1_finish<HOST, false>(a, tot[0], pre);
 }
 
 // K2.  The test runs when the iteration count is a multiple of k or reaches
