@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "cg_internal.hpp"
 #include "cluster_cg.hpp"
@@ -34,7 +35,7 @@ struct Shared {
   double* slot;               // this CTA's published partial sums, [2][4]
   double* const* peer_slot;   // the slot arrays of every CTA of the cluster, [C]
   void* red;                  // block-sum scratch, 4 * blockDim.x values
-  double* tot;                // broadcast of the totals, [4]
+  double* tot;                // broadcast of the totals and the scalars derived from them, [8]
   int C, rank;
 };
 
@@ -79,14 +80,24 @@ __device__ __forceinline__ void block_sum_quad(T (&v)[NV], T* smem) {
   }
 }
 
+struct NoScalars {
+  __device__ void operator()(double*) const {}
+};
+
 // Sum NV values over the cluster.  The CTA's block sums (block_sum_quad) go
 // to its slot, a cluster barrier publishes them, and every CTA adds the C
 // slots in rank order with the same warp tree, so all threads of all CTAs
 // get the same bits.
 // Slots alternate between two buffers: a buffer is rewritten only two sums
 // later, after a barrier that every CTA passes only once done reading it.
-template <int NV, class T>
-__device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& parity, cgx::cluster_group& cl) {
+// scalars(t) runs in thread 0 once the totals are in t[0 .. NV) and may store
+// further scalars derived from them in t[NV .. 8) (a division, a square root,
+// a decision), which reach every thread with the totals: computed by every
+// thread instead, each float64 operation would occupy every warp's
+// sub-partition pipe (about 64 cycles per warp instruction on GB300).
+template <int NV, class T, class Scalars = NoScalars>
+__device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& parity, cgx::cluster_group& cl,
+                                            Scalars scalars = Scalars()) {
   block_sum_quad<NV>(v, reinterpret_cast<T*>(S.red));
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -101,6 +112,7 @@ __device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& pa
       t = dev::warp_sum(t);
       if (lane == 0) S.tot[k] = (double)t;
     }
+    if (lane == 0) scalars(S.tot);
   }
   __syncthreads();
 #pragma unroll
@@ -112,7 +124,7 @@ __device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& pa
 struct Block {
   double slot[2][4];
   double red[4 * kClusterThreads];
-  double tot[4];
+  double tot[8];
   double* peer_slot[kMaxCluster];
   void* peer_data[2][kMaxCluster];  // the dynamic arrays of every CTA
   int sys;
@@ -182,6 +194,7 @@ __device__ __forceinline__ int pcg_loop(const Rows& g, const TV* __restrict__ va
                         T (&rk)[R], T (&zk)[R], const T (&dk)[R], T rho, T& rr, T tol, int max_it, int kchk,
                         const Shared& S, int& parity, cgx::cluster_group& cl, double* alpha_h, double* beta_h,
                         int hist_len, int* iters) {
+  constexpr bool kHoist = std::is_same<T, double>::value;
   T wk[R];
   int it = 0;
   int done = 0;
@@ -207,13 +220,31 @@ __device__ __forceinline__ int pcg_loop(const Rows& g, const TV* __restrict__ va
         gsum[0] = fma(s_p[loc], w, gsum[0]);
       }
     }
-    cluster_sum<1>(gsum, S, parity, cl);
-    const T gamma = gsum[0];
-    if (!(gamma > T(0)) || !isfinite(gamma)) {
-      done = kDoneBreakdown;
-      break;
+    // gamma = (p, w).  float64: thread 0 forms alpha = rho / gamma (t[1]) or flags a breakdown (t[2]) once
+    // for the CTA; float32 operations are cheap, every thread forms them (measured faster for the float32
+    // inner solves of the refinement kernel)
+    T alpha;
+    if constexpr (kHoist) {
+      cluster_sum<1>(gsum, S, parity, cl, [&](double* t) {
+        const T gamma = (T)t[0];
+        const bool bad = !(gamma > T(0)) || !isfinite(gamma);
+        t[1] = bad ? 0.0 : (double)(rho / gamma);
+        t[2] = bad ? 1.0 : 0.0;
+      });
+      if (S.tot[2] != 0.0) {
+        done = kDoneBreakdown;
+        break;
+      }
+      alpha = (T)S.tot[1];
+    } else {
+      cluster_sum<1>(gsum, S, parity, cl);
+      const T gamma = gsum[0];
+      if (!(gamma > T(0)) || !isfinite(gamma)) {
+        done = kDoneBreakdown;
+        break;
+      }
+      alpha = rho / gamma;
     }
-    const T alpha = rho / gamma;
     if (hist_len > 0 && it < hist_len && S.rank == 0 && threadIdx.x == 0) alpha_h[it] = alpha;
     ++it;
     const bool check = (it % kchk == 0) || it >= max_it;
@@ -229,20 +260,47 @@ __device__ __forceinline__ int pcg_loop(const Rows& g, const TV* __restrict__ va
         if (check) u[1] = fma(rk[k], rk[k], u[1]);
       }
     }
-    cluster_sum<2>(u, S, parity, cl);
-    const T rz = u[0];
-    if (check) rr = u[1];
-    if ((check && rr == T(0)) || rz == T(0))
-      done = kDoneConverged;
-    else if (check && sqrt(rr) <= tol)
-      done = kDoneConverged;
-    else if (it >= max_it)
-      done = kDoneNotConverged;
-    else if (!isfinite(rz) || (check && !isfinite(rr)))
-      done = kDoneBreakdown;
-    if (done) break;
-    const T beta = rz / rho;
-    rho = rz;
+    // (r, z) and, on test iterations, (r, r); thread 0 takes the decision (t[3]) and forms beta (t[2])
+    const T rr_prev = rr;
+    T beta;
+    if constexpr (!kHoist) {
+      cluster_sum<2>(u, S, parity, cl);
+      const T rz = u[0];
+      if (check) rr = u[1];
+      if ((check && rr == T(0)) || rz == T(0))
+        done = kDoneConverged;
+      else if (check && sqrt(rr) <= tol)
+        done = kDoneConverged;
+      else if (it >= max_it)
+        done = kDoneNotConverged;
+      else if (!isfinite(rz) || (check && !isfinite(rr)))
+        done = kDoneBreakdown;
+      if (done) break;
+      beta = rz / rho;
+      rho = rz;
+    } else {
+      cluster_sum<2>(u, S, parity, cl, [&](double* t) {
+        const T rz = (T)t[0];
+        const T rrn = check ? (T)t[1] : rr_prev;
+        int d = 0;
+        if ((check && rrn == T(0)) || rz == T(0))
+          d = kDoneConverged;
+        else if (check && sqrt(rrn) <= tol)
+          d = kDoneConverged;
+        else if (it >= max_it)
+          d = kDoneNotConverged;
+        else if (!isfinite(rz) || (check && !isfinite(rrn)))
+          d = kDoneBreakdown;
+        t[2] = d ? 0.0 : (double)(rz / rho);
+        t[3] = (double)d;
+      });
+      const T rz = u[0];
+      if (check) rr = u[1];
+      done = (int)S.tot[3];
+      if (done) break;
+      beta = (T)S.tot[2];
+      rho = rz;
+    }
     if (hist_len > 0 && it - 1 < hist_len && S.rank == 0 && threadIdx.x == 0) beta_h[it - 1] = beta;
 #pragma unroll
     for (int k = 0; k < R; ++k) {

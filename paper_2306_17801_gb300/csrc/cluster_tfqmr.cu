@@ -122,6 +122,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) tfqmr_cluster_kernel(Clust
         if (hist > 0 && S.rank == 0 && threadIdx.x == 0) a.alpha_h[0] = alpha;
       }
     }
+    // The scalar recurrences after each cluster sum run in thread 0 and reach every thread with the totals
+    // (clu::cluster_sum's scalars hook): computed by every thread, each float64 square root and division would
+    // occupy every warp's sub-partition pipe.  Same operations in the same order: the same bits.
     while (!done) {
       // odd half-step: u2 = u - alpha v, w -= alpha p, d = u + co d (after the pending x update)
       double ww[1] = {0.0};
@@ -135,12 +138,22 @@ __global__ void __launch_bounds__(kClusterThreads, 1) tfqmr_cluster_kernel(Clust
           ww[0] = fma(wk[k], wk[k], ww[0]);
           s_u2[threadIdx.x + k * blockDim.x] = u2k[k];
         }
-      clu::cluster_sum<1>(ww, S, parity, cl);  // also publishes u2
-      theta = sqrt(ww[0]) / tau;
-      double c = 1.0 / sqrt(1.0 + theta * theta);
-      tau = tau * theta * c;
-      eta = c * c * alpha;
-      if (!isfinite(theta) || !isfinite(tau)) {
+      // t: [1] theta, [2] tau, [3] eta, [4] co, [5] 1 = breakdown, 2 = quasi-residual zero
+      clu::cluster_sum<1>(ww, S, parity, cl, [&](double* t) {  // also publishes u2
+        const double th = sqrt(t[0]) / tau;
+        const double c = 1.0 / sqrt(1.0 + th * th);
+        const double ta = tau * th * c;
+        const double et = c * c * alpha;
+        t[1] = th;
+        t[2] = ta;
+        t[3] = et;
+        t[4] = th * th * et / alpha;
+        t[5] = (!isfinite(th) || !isfinite(ta)) ? 1.0 : ta == 0.0 ? 2.0 : 0.0;
+      });
+      theta = S.tot[1];
+      tau = S.tot[2];
+      eta = S.tot[3];
+      if (S.tot[5] == 1.0) {
         pending = false;
         ++it;
         done = kDoneBreakdown;
@@ -148,8 +161,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) tfqmr_cluster_kernel(Clust
       }
       eta_x = eta;
       pending = true;
-      co = theta * theta * eta / alpha;
-      if (tau == 0.0) {  // the quasi-residual vanished: x is exact after this half-step
+      co = S.tot[4];
+      if (S.tot[5] == 2.0) {  // the quasi-residual vanished: x is exact after this half-step
         ++it;
         done = kDoneConverged;
         break;
@@ -169,33 +182,48 @@ __global__ void __launch_bounds__(kClusterThreads, 1) tfqmr_cluster_kernel(Clust
           s2[0] = fma(wk[k], wk[k], s2[0]);
           s2[1] = fma(wk[k], rs[k], s2[1]);
         }
-      clu::cluster_sum<2>(s2, S, parity, cl);  // also publishes w
       ++it;
-      theta = sqrt(s2[0]) / tau;
-      c = 1.0 / sqrt(1.0 + theta * theta);
-      tau = tau * theta * c;
-      eta = c * c * alpha;
-      if (!isfinite(theta) || !isfinite(tau)) {
+      // t: [2] theta, [3] tau, [4] eta, [5] beta, [6] 1 = breakdown (before the pending update),
+      // 2 = converged, 3 = not converged, 4 = breakdown (after it)
+      clu::cluster_sum<2>(s2, S, parity, cl, [&](double* t) {  // also publishes w
+        const double th = sqrt(t[0]) / tau;
+        const double c = 1.0 / sqrt(1.0 + th * th);
+        const double ta = tau * th * c;
+        const double et = c * c * alpha;
+        t[2] = th;
+        t[3] = ta;
+        t[4] = et;
+        t[5] = 0.0;
+        const bool check = (it % a.check_every == 0) || it >= max_it;
+        double f = 0.0;
+        if (!isfinite(th) || !isfinite(ta))
+          f = 1.0;
+        else if (ta == 0.0 || (check && sqrt(2.0 * it + 1.0) * ta <= tol))
+          f = 2.0;
+        else if (it >= max_it)
+          f = 3.0;
+        else if (rho == 0.0 || !isfinite(t[1]))
+          f = 4.0;
+        else
+          t[5] = t[1] / rho;
+        t[6] = f;
+      });
+      theta = S.tot[2];
+      tau = S.tot[3];
+      eta = S.tot[4];
+      const double f = S.tot[6];
+      if (f == 1.0) {
         pending = false;
         done = kDoneBreakdown;
         break;
       }
       eta_x = eta;
       pending = true;
-      const bool check = (it % a.check_every == 0) || it >= max_it;
-      if (tau == 0.0 || (check && sqrt(2.0 * it + 1.0) * tau <= tol)) {
-        done = kDoneConverged;
+      if (f != 0.0) {
+        done = f == 2.0 ? kDoneConverged : f == 3.0 ? kDoneNotConverged : kDoneBreakdown;
         break;
       }
-      if (it >= max_it) {
-        done = kDoneNotConverged;
-        break;
-      }
-      if (rho == 0.0 || !isfinite(s2[1])) {
-        done = kDoneBreakdown;
-        break;
-      }
-      beta = s2[1] / rho;
+      beta = S.tot[5];
       rho = s2[1];
       if (it - 1 < hist && S.rank == 0 && threadIdx.x == 0) a.beta_h[it - 1] = beta;
       // directions: u = w + beta u2, p = M w + beta q, v = p + beta (q + beta v), sigma = (v, r*)
@@ -211,13 +239,20 @@ __global__ void __launch_bounds__(kClusterThreads, 1) tfqmr_cluster_kernel(Clust
           vk[k] = fma(beta, t, pk[k]);
           sg[0] = fma(vk[k], rs[k], sg[0]);
         }
-      clu::cluster_sum<1>(sg, S, parity, cl);
-      if (sg[0] == 0.0 || !isfinite(sg[0])) {
+      // t: [1] alpha, [2] co, [3] 1 = breakdown
+      clu::cluster_sum<1>(sg, S, parity, cl, [&](double* t) {
+        const bool bad = t[0] == 0.0 || !isfinite(t[0]);
+        const double al = bad ? 0.0 : rho / t[0];
+        t[1] = al;
+        t[2] = bad ? 0.0 : theta * theta * eta / al;
+        t[3] = bad ? 1.0 : 0.0;
+      });
+      if (S.tot[3] != 0.0) {
         done = kDoneBreakdown;
         break;
       }
-      alpha = rho / sg[0];
-      co = theta * theta * eta / alpha;
+      alpha = S.tot[1];
+      co = S.tot[2];
       if (it < hist && S.rank == 0 && threadIdx.x == 0) a.alpha_h[it] = alpha;
     }
 #pragma unroll
