@@ -244,6 +244,17 @@ def test_launch_floor_reports_positive_times(dev):
     apcg.call("apcg_ctx_destroy", C.c_void_p(ctx))
 
 
+def test_fp64_fma_peak_is_in_the_float64_range(dev):
+    """Independent float64 FMA chains: GB300's float64 pipe is 2 lanes/SM/cycle (152 SMs, up to 2.07 GHz: at
+    most 1.26 TFLOP/s); a figure far above means the kernel's FMAs were folded away, far below that it stalls."""
+    ctx = apcg.ctx_create()
+    g = apcg.fp64_fma_peak(ctx, 2)
+    assert 300.0 < g < 1.6e3, g
+    with pytest.raises(apcg.ApcgError):
+        apcg.fp64_fma_peak(ctx, 0)
+    apcg.call("apcg_ctx_destroy", C.c_void_p(ctx))
+
+
 def test_views_keep_their_tensors_alive(dev):
     """The library holds raw device pointers; the binding keeps each wrapped tensor until its view is destroyed."""
     import gc
