@@ -304,8 +304,10 @@ __device__ __forceinline__ void grid_partials_exact(const double* partials, doub
 // Deterministic grid-wide sum of NV values per thread.  Each block writes its
 // NV block sums to partials[k * gridDim.x + blockIdx.x]; the block that
 // arrives last (one acquire-release ticket increment) sums the partials and
-// returns true; only its thread 0 holds valid totals in tot[].  The ticket is
-// reset to zero for the next kernel.  partials must hold NV * gridDim.x values
+// returns true; only its thread 0 holds valid totals in tot[].  arrival, when
+// given, receives the block's arrival index (0 .. gridDim.x - 1, the last block
+// gridDim.x - 1) in every thread.  The ticket is reset to zero for the next
+// kernel.  partials must hold NV * gridDim.x values
 // and smem NV * blockDim.x values.  float64 block sums take the exact integer
 // path above when kBlockExact; the last block's sum of the partials takes it
 // when kGridExact, and otherwise is a float64 tree in block order.  float32
@@ -320,9 +322,11 @@ constexpr bool kBlockExact = APCG_BLOCK_EXACT != 0;
 constexpr bool kGridExact = APCG_GRID_EXACT != 0;
 
 template <int NV, class T>
-__device__ __forceinline__ bool grid_sum_last(T (&v)[NV], T* partials, unsigned int* ticket, T* smem, T (&tot)[NV]) {
+__device__ __forceinline__ bool grid_sum_last(T (&v)[NV], T* partials, unsigned int* ticket, T* smem, T (&tot)[NV],
+                                              unsigned* arrival = nullptr) {
   constexpr bool f64 = std::is_same<T, double>::value;
   __shared__ bool s_last;
+  __shared__ unsigned s_arrival;
   if constexpr (f64 && kBlockExact)
     block_sum_exact<NV>(v, smem);
   else
@@ -336,8 +340,10 @@ __device__ __forceinline__ bool grid_sum_last(T (&v)[NV], T* partials, unsigned 
     unsigned t;
     asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(ticket) : "memory");
     s_last = (t == gridDim.x - 1);
+    if (arrival) s_arrival = t;
   }
   __syncthreads();
+  if (arrival) *arrival = s_arrival;
   if (!s_last) return false;
   if constexpr (f64 && kGridExact) {
     grid_partials_exact<NV>(reinterpret_cast<const double*>(partials), reinterpret_cast<double*>(smem),
