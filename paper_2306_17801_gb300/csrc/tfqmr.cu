@@ -22,8 +22,13 @@
 // of w, which is complete when T2 ends, instead of that of u, which T3
 // itself produces; it saves a kernel and a grid-wide boundary per iteration
 // and changes only the rounding.  The update x += eta d of a half-step needs
-// eta from that half-step's reduction, so it is applied by the next kernel
-// that rewrites d (or, when the solve stops, by a finish kernel).
+// eta from that half-step's reduction, so it is applied by the next
+// half-step (or, when the solve stops, by a finish kernel).  d lives in two
+// buffers that the half-steps alternate (T1 reads d and writes d2, T2 reads d2
+// and writes d), so the pending update still finds its d after the sweep has
+// written the new one: each half-step applies it once the block's partial sums
+// are out, every block but the last on the slice of x of its arrival index,
+// while the last block runs the serial tail of the reduction.
 //
 // An iteration reads the matrix twice (two SpMVs) and reduces four inner
 // products at three points, against one SpMV and two or three products for
@@ -52,6 +57,9 @@ namespace apcg {
 namespace tq {
 
 constexpr int kThreads = 256;
+// 16-byte vectors per thread and array in flight in the x updates that follow a ticket (more spill: T1 at
+// 64 registers with 4, the one-entry-at-a-time T2 at 40 registers with more than 2)
+constexpr int kXvT1 = 2, kXvT2 = 4, kXvT2Single = 2;
 constexpr int kClusterMaxRows = 16384;  // the whole-solve cluster kernel: 16 CTAs x 512 threads x 2 rows
 
 // Device-resident scalars of one TFQMR solve.
@@ -66,7 +74,7 @@ struct TqState {
   int32_t iter;    // completed iterations
   int32_t done;    // kDone*
   int32_t max_it, check_every, hist_len;
-  int32_t pending;  // eta_x holds an update not yet applied to x
+  int32_t pending;  // eta_x holds an update not yet applied to x: 0 none, 1 along d, 2 along d2
   int32_t body_runs;
   unsigned int ticket;
 };
@@ -80,7 +88,8 @@ struct TqArgs {
   double* u;
   double* u2;
   double* w;
-  double* d;
+  double* d;   // written by T2 (and zeroed by S1), read by T1
+  double* d2;  // written by T1, read by T2
   double* v;
   double* p;
   double* q;
@@ -98,9 +107,10 @@ struct HostScalars {
 
 __device__ __forceinline__ int32_t read_done(const TqState* st) { return *(volatile const int32_t*)&st->done; }
 
-// The quasi-residual update after a half-step (last block, device mode).
+// The quasi-residual update after a half-step (last block, device mode); buf:
+// the pending code of the d buffer that the half-step wrote (1: d, 2: d2).
 // Returns false on a non-finite value.
-__device__ __forceinline__ bool quasi_update(TqState* st, double ww) {
+__device__ __forceinline__ bool quasi_update(TqState* st, double ww, int32_t buf) {
   const double theta = sqrt(ww) / st->tau;
   const double c = 1.0 / sqrt(1.0 + theta * theta);
   const double tau = st->tau * theta * c;
@@ -109,8 +119,44 @@ __device__ __forceinline__ bool quasi_update(TqState* st, double ww) {
   st->tau = tau;
   st->eta = eta;
   st->eta_x = eta;
-  st->pending = 1;
+  st->pending = buf;
   return isfinite(theta) && isfinite(tau);
+}
+
+// x += ex dd over the slice of [0, n) of this block's arrival index, after a grid reduction's ticket: every
+// block but the one that arrived last takes one of gridDim.x - 1 slices (a grid of one block takes all), so the
+// bytes move while the last block finishes the reduction.  The element left over by the 16-byte vectors of an
+// odd n goes to the block that arrived first.
+// V: 16-byte vectors per thread and array in flight.
+template <int V>
+__device__ __forceinline__ void x_update_slice(double* __restrict__ x, const double* __restrict__ dd, double ex,
+                                               int64_t n, unsigned arrival, bool last) {
+  if (last && gridDim.x > 1) return;
+  const int64_t nv = n / 2, parts = gridDim.x > 1 ? (int64_t)gridDim.x - 1 : 1;
+  const int64_t lo = nv * (int64_t)arrival / parts, hi = nv * ((int64_t)arrival + 1) / parts;
+  double2* xv = reinterpret_cast<double2*>(x);
+  const double2* dv = reinterpret_cast<const double2*>(dd);
+  for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += V * kThreads) {
+    double2 xx[V], de[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      if (i < hi) {
+        xx[u] = xv[i];
+        de[u] = __ldg(dv + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t i = i0 + u * kThreads;
+      if (i < hi) {
+        xx[u].x = fma(ex, de[u].x, xx[u].x);
+        xx[u].y = fma(ex, de[u].y, xx[u].y);
+        xv[i] = xx[u];
+      }
+    }
+  }
+  if (arrival == 0 && threadIdx.x == 0 && (n & 1)) x[n - 1] = fma(ex, dd[n - 1], x[n - 1]);
 }
 
 // S1: r0 = D^-1 (b - A x0);  u = w = r* = r0;  d = 0;  ||r0||^2, ||D^-1 b||^2;
@@ -193,22 +239,16 @@ __global__ void __launch_bounds__(kThreads, 4) t1_kernel(TqArgs a, HostScalars h
   __shared__ double red[kThreads];
   double acc = 0.0;
   const int64_t n = a.n, nv = n / 2, stride = (int64_t)gridDim.x * blockDim.x;
-  double2* xv = reinterpret_cast<double2*>(a.x);
   const double2* uv = reinterpret_cast<const double2*>(a.u);
   const double2* vv = reinterpret_cast<const double2*>(a.v);
   const double2* pv = reinterpret_cast<const double2*>(a.p);
   double2* wv = reinterpret_cast<double2*>(a.w);
-  double2* dv = reinterpret_cast<double2*>(a.d);
+  const double2* dv = reinterpret_cast<const double2*>(a.d);
+  double2* d2v = reinterpret_cast<double2*>(a.d2);
   double2* u2v = reinterpret_cast<double2*>(a.u2);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
     const double2 uu = dev::ld_stream2(uv + i), vvv = dev::ld_stream2(vv + i), pp = dev::ld_stream2(pv + i);
-    double2 ww = wv[i], dd = dv[i], u2;
-    if (pend) {
-      double2 xx = xv[i];
-      xx.x = fma(ex, dd.x, xx.x);
-      xx.y = fma(ex, dd.y, xx.y);
-      xv[i] = xx;
-    }
+    double2 ww = wv[i], dd = __ldg(dv + i), u2;
     u2.x = fma(-alpha, vvv.x, uu.x);
     u2.y = fma(-alpha, vvv.y, uu.y);
     ww.x = fma(-alpha, pp.x, ww.x);
@@ -219,22 +259,24 @@ __global__ void __launch_bounds__(kThreads, 4) t1_kernel(TqArgs a, HostScalars h
     acc = fma(ww.y, ww.y, acc);
     u2v[i] = u2;
     wv[i] = ww;
-    dv[i] = dd;
+    d2v[i] = dd;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {
     const int64_t i = n - 1;
-    if (pend) a.x[i] = fma(ex, a.d[i], a.x[i]);
     a.u2[i] = fma(-alpha, a.v[i], a.u[i]);
     a.w[i] = fma(-alpha, a.p[i], a.w[i]);
-    a.d[i] = fma(co, a.d[i], a.u[i]);
+    a.d2[i] = fma(co, a.d[i], a.u[i]);
     acc = fma(a.w[i], a.w[i], acc);
   }
   double v[1] = {acc}, tot[1];
-  if (dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+  unsigned arrival;
+  const bool last = dev::grid_sum_last<1>(v, a.partials, &a.st->ticket, red, tot, &arrival);
+  if (pend) x_update_slice<kXvT1>(a.x, a.d, ex, n, arrival, last);
+  if (last && threadIdx.x == 0) {
     TqState* st = a.st;
     st->ww = tot[0];
     if (!HOST) {
-      if (!quasi_update(st, tot[0])) {
+      if (!quasi_update(st, tot[0], 2)) {
         st->pending = 0;
         st->iter += 1;  // the iteration stopped inside its first half-step
         st->done = kDoneBreakdown;
@@ -273,18 +315,18 @@ __global__ void __launch_bounds__(kThreads, G == 0 ? 6 : 4) t2_kernel(TqArgs a, 
   double v[2] = {0.0, 0.0};
   dev::sell_spmv<true, (G > 0), double, (G > 0 ? G : 8), CF>(a.A, a.u2, [&](int32_t i, double au2, double u2i) {
                                           const double qi = __ldg(a.dinv + i) * au2;
-                                          double di = a.d[i];
-                                          if (pend) a.x[i] = fma(ex, di, a.x[i]);
                                           const double wi = fma(-alpha, qi, a.w[i]);
-                                          di = fma(co, di, u2i);
                                           a.q[i] = qi;
                                           a.w[i] = wi;
-                                          a.d[i] = di;
+                                          a.d[i] = fma(co, __ldg(a.d2 + i), u2i);
                                           v[0] = fma(wi, wi, v[0]);
                                           v[1] = fma(wi, __ldg(a.rs + i), v[1]);
                                         });
   double tot[2];
-  if (dev::grid_sum_last<2>(v, a.partials, &a.st->ticket, red, tot) && threadIdx.x == 0) {
+  unsigned arrival;
+  const bool last = dev::grid_sum_last<2>(v, a.partials, &a.st->ticket, red, tot, &arrival);
+  if (pend) x_update_slice<(G == 0 ? kXvT2Single : kXvT2)>(a.x, a.d2, ex, a.n, arrival, last);
+  if (last && threadIdx.x == 0) {
     TqState* st = a.st;
     st->ww = tot[0];
     st->wr = tot[1];
@@ -292,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, G == 0 ? 6 : 4) t2_kernel(TqArgs a, 
       const int32_t it = st->iter + 1;
       st->iter = it;
       int32_t done = 0;
-      if (!quasi_update(st, tot[0])) {
+      if (!quasi_update(st, tot[0], 1)) {
         st->pending = 0;
         done = kDoneBreakdown;
       } else {
@@ -355,14 +397,16 @@ __global__ void __launch_bounds__(kThreads) t3_kernel(TqArgs a, HostScalars h) {
   }
 }
 
-// The update still pending when the iteration stops: x += eta_x d.
+// The update still pending when the iteration stops: x += eta_x d, along the
+// d buffer that the stopping half-step wrote.
 __global__ void __launch_bounds__(kThreads) finish_kernel(TqArgs a, HostScalars h, int32_t host) {
-  const bool pend = host ? h.pending != 0 : a.st->pending != 0;
-  if (!pend) return;
+  const int32_t pend = host ? h.pending : a.st->pending;
+  if (pend != 1 && pend != 2) return;
   const double ex = host ? h.eta_x : a.st->eta_x;
+  const double* __restrict__ dd = pend == 2 ? a.d2 : a.d;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
-    a.x[i] = fma(ex, a.d[i], a.x[i]);
+    a.x[i] = fma(ex, dd[i], a.x[i]);
 }
 
 template <class K>
@@ -380,14 +424,14 @@ int occupancy_grid(K kernel, int sms, int64_t want) {
 
 // The host's copy of the quasi-residual update (host-synchronous form); the
 // same operations in the same order as quasi_update.
-bool host_quasi_update(TqState* h, double ww) {
+bool host_quasi_update(TqState* h, double ww, int32_t buf) {
   const double theta = std::sqrt(ww) / h->tau;
   const double c = 1.0 / std::sqrt(1.0 + theta * theta);
   h->tau = h->tau * theta * c;
   h->theta = theta;
   h->eta = c * c * h->alpha;
   h->eta_x = h->eta;
-  h->pending = 1;
+  h->pending = buf;
   return std::isfinite(theta) && std::isfinite(h->tau);
 }
 
@@ -587,7 +631,7 @@ apcg_status solve_host_sync(Plan P, const double* b, double* x) {
     APCG_TRY(launch_t1(P, x, s, true, scal()));
     launches++;
     APCG_TRY(read_state(P, s));
-    if (!host_quasi_update(&m, h->ww)) {
+    if (!host_quasi_update(&m, h->ww, 2)) {
       m.pending = 0;
       done = kDoneBreakdown;
       break;
@@ -601,7 +645,7 @@ apcg_status solve_host_sync(Plan P, const double* b, double* x) {
     launches++;
     APCG_TRY(read_state(P, s));
     const double wr = h->wr;
-    if (!host_quasi_update(&m, h->ww)) {
+    if (!host_quasi_update(&m, h->ww, 1)) {
       m.pending = 0;
       done = kDoneBreakdown;
       break;
@@ -861,7 +905,7 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   P->grid_spmv = occupancy_grid(t2_for(false, cf, P->group), sms, (slices + 7) / 8);
   P->grid_t3 = occupancy_grid(t3_for(false, cf, P->group), sms, (slices + 7) / 8);
   P->grid_vec = occupancy_grid(t1_kernel<false>, sms, ((int64_t)P->n / 2 + kThreads - 1) / kThreads);
-  // Workspace: dinv, r*, u, u2, w, d, v, p, q; partials; state; histories; sliced-ELL copy.
+  // Workspace: dinv, r*, u, u2, w, d, d2, v, p, q; partials; state; histories; sliced-ELL copy.
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nv = up(sizeof(double) * (size_t)(P->n > 0 ? P->n : 1));
   const size_t npart = up(sizeof(double) * dev::kMaxPartials * 2);
@@ -874,12 +918,12 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
                              : (d16 ? sizeof(int16_t) : sizeof(int32_t)) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nval = up(sizeof(double) * (size_t)std::max<int64_t>(L.padded, 1));
   const size_t nsysb = up(sizeof(SysDesc) + sizeof(SysResult) + 64);
-  const size_t total = 9 * nv + npart + nst + 2 * nh + nsptr + ncol + nval + nsysb;
+  const size_t total = 10 * nv + npart + nst + 2 * nh + nsptr + ncol + nval + nsysb;
   char* ws = nullptr;
   APCG_TRY(dev_alloc_async((void**)&ws, total, ctx->stream));
   P->ws = ws;
-  double* vecs[9];
-  for (int i = 0; i < 9; ++i) vecs[i] = reinterpret_cast<double*>(ws + i * nv);
+  double* vecs[10];
+  for (int i = 0; i < 10; ++i) vecs[i] = reinterpret_cast<double*>(ws + i * nv);
   TqArgs& a = P->a;
   a.n = P->n;
   a.dinv = vecs[0];
@@ -888,10 +932,11 @@ apcg_status plan_create(apcg_ctx ctx, apcg_mat A, const apcg_cg_opts* opts, Plan
   a.u2 = vecs[3];
   a.w = vecs[4];
   a.d = vecs[5];
+  a.d2 = vecs[9];
   a.v = vecs[6];
   a.p = vecs[7];
   a.q = vecs[8];
-  char* q = ws + 9 * nv;
+  char* q = ws + 10 * nv;
   a.partials = reinterpret_cast<double*>(q);
   a.st = reinterpret_cast<TqState*>(q + npart);
   a.alpha_h = reinterpret_cast<double*>(q + npart + nst);
