@@ -221,9 +221,18 @@ __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
     k1_finish<HOST, STAGED>(a, tot[0], STAGED ? *a.st : pre);
 }
 
-// K1 on a stencil operator (stencil.cuh): the same per-row arithmetic.
+// K1 on a stencil operator (stencil.cuh): the same per-row arithmetic.  Resident blocks per SM by term
+// count: the 7-term instance at one (the compiler then keeps more gathers in flight on 78 registers, three
+// blocks per SM: 128^3 K1 44.0 -> 42.4 us against 48 registers and five), the 27-term one at three (80
+// registers; 128 and two blocks 1% slower, 64 and four 2% slower), the others where their register counts
+// were before these bounds.
+template <int NP>
+constexpr int stencil_min_blocks() {
+  return NP == 7 ? 1 : NP == 27 ? 3 : NP == 9 ? 5 : NP == 0 ? 2 : 6;
+}
 template <bool HOST, int NP, class T>
-__global__ void __launch_bounds__(kThreads) k1_stencil_kernel(Args<T> a, dev::StencilView S) {
+__global__ void __launch_bounds__(kThreads, stencil_min_blocks<NP>()) k1_stencil_kernel(Args<T> a,
+                                                                                       dev::StencilView S) {
   if (!HOST && read_done(a.st)) return;
   __shared__ __align__(16) CgState pre;
   if (!HOST) state_prefetch(a.st, &pre);
@@ -520,8 +529,12 @@ void core_configure(CgCore<T>& c, int64_t nnz, int sms) {
   const int64_t slices = ((int64_t)c.n + 31) / 32;
   const int64_t spmv_blocks = (slices + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t vec_blocks = (((int64_t)c.n / V16<T>::E) + (int64_t)kThreads * kUpdV - 1) / ((int64_t)kThreads * kUpdV);
-  if (c.S.n > 0)
-    c.grid_spmv = occupancy_grid((void*)k1_stencil_kernel<false, 7, T>, sms, ((int64_t)c.n + kThreads - 1) / kThreads);
+  if (c.S.n > 0) {  // the grid of the instance that runs (one resident wave)
+    void* ks = c.S.npts == 5 ? (void*)k1_stencil_kernel<false, 5, T> : c.S.npts == 7 ? (void*)k1_stencil_kernel<false, 7, T>
+             : c.S.npts == 9 ? (void*)k1_stencil_kernel<false, 9, T> : c.S.npts == 27 ? (void*)k1_stencil_kernel<false, 27, T>
+             : (void*)k1_stencil_kernel<false, 0, T>;
+    c.grid_spmv = occupancy_grid(ks, sms, ((int64_t)c.n + kThreads - 1) / kThreads);
+  }
   else {
     const int dyn = k1_dyn_smem(c);
     if (dyn > 48 * 1024) {  // above the default limit: opt in (both instances, once per plan)
