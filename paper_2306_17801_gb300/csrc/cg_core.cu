@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
     extern __shared__ __align__(128) unsigned char stage_smem[];
     const int w = threadIdx.x >> 5;
     uint64_t* bars = reinterpret_cast<uint64_t*>(stage_smem) + 2 * w;
-    unsigned char* wsm = stage_smem + dev::kStageBarrierBytes + (size_t)w * dev::stage_warp_bytes(a.A.stage_cap);
-    dev::sell_spmv_staged<true, G>(a.A, a.p, wsm, bars, &a.st->done, kDoneTimeout, epi);
+    float* stage = reinterpret_cast<float*>(stage_smem + dev::kStageBarrierBytes) + (size_t)w * 2 * a.A.stage_cap * 32;
+    dev::sell_spmv_staged<true, G>(a.A, a.p, stage, bars, &a.st->done, kDoneTimeout, epi);
   } else {
     dev::sell_spmv<true, LONG, T, G, CF>(a.A, a.p, epi);
   }

@@ -209,19 +209,9 @@ constexpr int kStageMaxWidth = 27;                // entries per row of the wide
 constexpr uint32_t kStageSpinLimit = 1u << 16;    // try_wait polls before a wait gives up (about 0.16 s)
 constexpr int kStageBarrierBytes = 128;           // mbarriers at the front of the dynamic shared memory
 
-// The gathered vector is staged too: for each slice the warp also copies the windows of x that its rows
-// reach, one window per run of offsets at most kStageRunGap apart (a 27-point slice: nine windows of 34
-// entries and their alignment, the 3 x 3 lines of neighbours), and reads x from shared memory.  A slice whose
-// windows exceed kStageWinCap floats, or whose last window would end past the last whole 16 bytes of x,
-// gathers x from global memory instead.
-constexpr int kStageWinCap = 448;  // floats of x windows per slice buffer
-constexpr int kStageRunGap = 4;    // offsets at most this far apart share a window
-
-// Dynamic shared memory of the staged K1: per warp two slice buffers of values, two of x windows, two
-// tables of (offset, window shift) per entry, and two mbarriers.
+// Dynamic shared memory of the staged K1: two slice buffers and two mbarriers per warp.
 __host__ __device__ constexpr int stage_smem_bytes(int cap, int warps) {
-  return kStageBarrierBytes + warps * 2 * (cap * 32 * (int)sizeof(float) + kStageWinCap * (int)sizeof(float) +
-                                           32 * (int)sizeof(int2));
+  return kStageBarrierBytes + warps * 2 * cap * 32 * (int)sizeof(float);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -230,18 +220,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// A bulk copy of bytes (a multiple of 16; both addresses 16-byte aligned) from global to shared memory that
-// completes that many bytes of the transaction announced on bar (mbar_expect).
-__device__ __forceinline__ void bulk_copy_tx(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// Bulk copy of bytes (a multiple of 16; both addresses 16-byte aligned) from global to shared memory,
+// completing a transaction of that many bytes on bar (one arrival by the calling thread, which announces
+// bytes + extra: extra is 0 except under the test hook SellView::stage_tx_extra).
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint32_t extra) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes + extra)
+               : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
                "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
-}
-
-// One arrival on bar announcing bytes of transaction.
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -264,82 +253,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// Bytes of one warp's part of the staged K1's dynamic shared memory (after the mbarriers).
-__host__ __device__ constexpr int stage_warp_bytes(int cap) {
-  return 2 * (cap * 32 * (int)sizeof(float) + kStageWinCap * (int)sizeof(float) + 32 * (int)sizeof(int2));
-}
-
-// Issue the copies of slice s (entries [b, e), rows 32 s ..) into one buffer: its values (lane 0) and, where
-// they fit, the windows of x that its rows reach (lane j: window j), all completing on bar; tab receives,
-// per entry k, the slice's offset o_k and the shift d_k such that x[c] sits at win[c + d_k] for every column
-// c = clamp(row + o_k) of that entry.  Returns whether the windows were staged.  All 32 lanes call this.
-__device__ __forceinline__ bool stage_slice(const SellView<float>& A, const float* __restrict__ x, bool x_ok,
-                                            int64_t s, int32_t b, int32_t e, float* vals, float* win, int2* tab,
-                                            uint64_t* bar) {
-  const int lane = threadIdx.x & 31;
-  const int32_t w = (e - b) >> 5;
-  const int32_t n = A.n, last = n - 1, row0 = (int32_t)(s * 32);
-  const int32_t o = lane < w ? __ldg(A.poff + (b >> 5) + lane) : 0;
-  const int32_t o_prev = __shfl_up_sync(kFull, o, 1);
-  const unsigned starts = __ballot_sync(kFull, lane < w && (lane == 0 || o - o_prev > kStageRunGap));
-  const int nruns = __popc(starts);
-  // window of run lane (lanes < nruns): entries [k0, k1]
-  int32_t lo = 0, size = 0;
-  {
-    const int k0 = lane < nruns ? (int)__fns(starts, 0, lane + 1) : 0;
-    const int k1 = lane + 1 < nruns ? (int)__fns(starts, 0, lane + 2) - 1 : w - 1;
-    const int32_t o0 = __shfl_sync(kFull, o, k0 & 31), o1 = __shfl_sync(kFull, o, k1 & 31);
-    if (lane < nruns) {
-      lo = min(max(row0 + o0, 0), last) & ~3;
-      int32_t hi = min(max(row0 + o1 + 32, lo + 1), n);
-      hi = (hi + 3) & ~3;
-      size = hi - lo;
-    }
-  }
-  // window bases: exclusive prefix sum of the sizes
-  int32_t incl = size;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int32_t t = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += t;
-  }
-  const int32_t total = __shfl_sync(kFull, incl, 31);
-  const int32_t end_max = __reduce_max_sync(kFull, (unsigned)(lo + size));
-  const bool xs = x_ok && nruns > 0 && total <= kStageWinCap && end_max <= (n & ~3);
-  // per entry: its run, then the shift from a column to its place in the windows
-  const int rid = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
-  const int32_t shift = (incl - size) - lo;  // window base minus window start, for run lane
-  const int32_t d = __shfl_sync(kFull, shift, rid < 0 ? 0 : rid);
-  if (lane < w) tab[lane] = make_int2(o, d);
-  const uint32_t vbytes = (uint32_t)(e - b) * 4u;
-  if (lane == 0) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect(bar, vbytes + (xs ? (uint32_t)total * 4u : 0u) + A.stage_tx_extra);
-  }
-  __syncwarp();
-  if (lane == 0) bulk_copy_tx(vals, A.val + b, vbytes, bar);
-  if (xs && lane < nruns) bulk_copy_tx(win + (incl - size), x + lo, (uint32_t)size * 4u, bar);
-  return xs;
-}
-
-// sell_spmv for float32 values and kColPattern with the values and the gathered vector staged as above.
-// wsm is this warp's part of the dynamic shared memory (stage_warp_bytes), bars its two mbarriers.  Slices
-// wider than A.stage_cap read their values and x from global memory.  A wait that gives up sets *fail to
-// fail_code, lets the warp's copies in flight land (bounded again) and ends the warp's sweep.  All 32 lanes
-// must call this function together.
+// sell_spmv for float32 values and kColPattern with the values staged as above.  stage holds this warp's two
+// buffers of A.stage_cap * 32 floats, bars its two mbarriers.  Slices wider than A.stage_cap read their
+// values from global memory.  A wait that gives up sets *fail to fail_code, lets the warp's copies in flight
+// land (bounded again) and ends the warp's sweep.  All 32 lanes must call this function together.
 template <bool OWN_X, int G, class Epi>
-__device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const float* __restrict__ x,
-                                                 unsigned char* wsm, uint64_t* bars, int32_t* fail, int32_t fail_code,
-                                                 Epi epi) {
+__device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const float* __restrict__ x, float* stage,
+                                                 uint64_t* bars, int32_t* fail, int32_t fail_code, Epi epi) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int32_t cap_entries = A.stage_cap * 32;
   const int32_t last = A.n - 1;
-  float* vals = reinterpret_cast<float*>(wsm);                   // [2][cap_entries]
-  float* wins = vals + 2 * cap_entries;                          // [2][kStageWinCap]
-  int2* tabs = reinterpret_cast<int2*>(wins + 2 * kStageWinCap);  // [2][32]
-  const bool x_ok = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
   if (lane == 0) {
     mbar_init(&bars[0]);
     mbar_init(&bars[1]);
@@ -360,21 +285,22 @@ __device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const
   uint32_t pending = 0u;  // bit b: a copy into buffer b has been issued and not waited for
   int buf = 0;            // buffer of the current slice
   bool cur_staged = gwarp < A.nslices && e_cur > b_cur && e_cur - b_cur <= cap_entries;
-  bool cur_xs = false;
   if (cur_staged) {
-    cur_xs = stage_slice(A, x, x_ok, gwarp, b_cur, e_cur, vals, wins, tabs, &bars[0]);
+    if (lane == 0) bulk_to_smem(stage, A.val + b_cur, (uint32_t)(e_cur - b_cur) * 4u, &bars[0], A.stage_tx_extra);
     pending |= 1u;
   }
   bool failed = false;
   for (int64_t s = gwarp; s < A.nslices; s += nwarps) {
-    // the next slice into the other buffer (its previous contents were consumed before the __syncwarp that
-    // ended the last step)
+    // the next slice's values into the other buffer (its previous contents were consumed before the
+    // __syncwarp that ended the last step)
     const bool has_next = s + nwarps < A.nslices;
     const bool nx_staged = has_next && e_nx > b_nx && e_nx - b_nx <= cap_entries;
-    bool nx_xs = false;
     if (nx_staged) {
-      nx_xs = stage_slice(A, x, x_ok, s + nwarps, b_nx, e_nx, vals + (buf ^ 1) * cap_entries,
-                          wins + (buf ^ 1) * kStageWinCap, tabs + (buf ^ 1) * 32, &bars[buf ^ 1]);
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_to_smem(stage + (buf ^ 1) * cap_entries, A.val + b_nx, (uint32_t)(e_nx - b_nx) * 4u, &bars[buf ^ 1],
+                     A.stage_tx_extra);
+      }
       pending |= 1u << (buf ^ 1);
     }
     if (s + 2 * nwarps < A.nslices) {
@@ -384,8 +310,9 @@ __device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const
     const int32_t row = (int32_t)(s * 32 + lane);
     float x_own = 0.f;
     if (OWN_X && row < A.n) x_own = ld_ro(x + row);
+    const int32_t* op = A.poff + (b_cur >> 5);
     const int32_t width = (e_cur - b_cur) >> 5;
-    float acc = 0.f;
+    const float* sv;
     if (cur_staged) {
       const bool ok = mbar_wait(&bars[buf], (parity >> buf) & 1u);
       if (!__all_sync(kFull, ok)) {  // the copy stays pending, with its phase's parity
@@ -394,58 +321,23 @@ __device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const
       }
       parity ^= 1u << buf;
       pending &= ~(1u << buf);
-      const float* sv = vals + buf * cap_entries + lane;
-      const int2* tb = tabs + buf * 32;
-      if (cur_xs) {
-        const float* wb = wins + buf * kStageWinCap;
-        int32_t k = 0;
-        for (; k + G <= width; k += G) {
-          int32_t j[G];
-          float xv[G];
-#pragma unroll
-          for (int g = 0; g < G; ++g) {
-            const int2 t = tb[k + g];
-            j[g] = min(max(row + t.x, 0), last) + t.y;
-          }
-#pragma unroll
-          for (int g = 0; g < G; ++g) xv[g] = wb[j[g]];
-#pragma unroll
-          for (int g = 0; g < G; ++g) acc = fmaf(sv[32 * (k + g)], xv[g], acc);
-        }
-        for (; k < width; ++k) {
-          const int2 t = tb[k];
-          acc = fmaf(sv[32 * k], wb[min(max(row + t.x, 0), last) + t.y], acc);
-        }
-      } else {
-        int32_t k = 0;
-        for (; k + G <= width; k += G) {
-          int32_t j[G];
-          float xv[G];
-#pragma unroll
-          for (int g = 0; g < G; ++g) j[g] = min(max(row + tb[k + g].x, 0), last);
-#pragma unroll
-          for (int g = 0; g < G; ++g) xv[g] = ld_ro(x + j[g]);
-#pragma unroll
-          for (int g = 0; g < G; ++g) acc = fmaf(sv[32 * (k + g)], xv[g], acc);
-        }
-        for (; k < width; ++k) acc = fmaf(sv[32 * k], ld_ro(x + min(max(row + tb[k].x, 0), last)), acc);
-      }
+      sv = stage + buf * cap_entries + lane;
     } else {
-      const int32_t* op = A.poff + (b_cur >> 5);
-      const float* sv = A.val + b_cur + lane;
-      int32_t k = 0;
-      for (; k + G <= width; k += G) {
-        int32_t j[G];
-        float xv[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) j[g] = min(max(row + __ldg(op + k + g), 0), last);
-#pragma unroll
-        for (int g = 0; g < G; ++g) xv[g] = ld_ro(x + j[g]);
-#pragma unroll
-        for (int g = 0; g < G; ++g) acc = fmaf(sv[32 * (k + g)], xv[g], acc);
-      }
-      for (; k < width; ++k) acc = fmaf(sv[32 * k], ld_ro(x + min(max(row + __ldg(op + k), 0), last)), acc);
+      sv = A.val + b_cur + lane;
     }
+    float acc = 0.f;
+    int32_t k = 0;
+    for (; k + G <= width; k += G) {
+      int32_t j[G];
+      float xv[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) j[g] = min(max(row + __ldg(op + k + g), 0), last);
+#pragma unroll
+      for (int g = 0; g < G; ++g) xv[g] = ld_ro(x + j[g]);
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc = fmaf(sv[32 * (k + g)], xv[g], acc);
+    }
+    for (; k < width; ++k) acc = fmaf(sv[32 * k], ld_ro(x + min(max(row + __ldg(op + k), 0), last)), acc);
     if (row < A.n) epi(row, acc, x_own);
     __syncwarp();
     buf ^= 1;
@@ -454,7 +346,6 @@ __device__ __forceinline__ void sell_spmv_staged(const SellView<float>& A, const
     b_nx = b_far;
     e_nx = e_far;
     cur_staged = nx_staged;
-    cur_xs = nx_xs;
   }
   if (failed) {
     if (lane == 0) atomicMax(fail, fail_code);
