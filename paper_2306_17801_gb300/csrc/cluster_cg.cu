@@ -30,9 +30,12 @@ namespace {
 
 using clu::cgx::cluster_group;
 
-// Shared-memory bookkeeping common to both kernels; returns the Shared view.
+// Float64 Jacobi-PCG, one cluster per system.  Two CTAs per SM up to R = 4: at 128 registers the R = 4
+// instance left one CTA, i.e. one system's cluster, per SM, and every cluster sum and barrier of that system
+// idled the SM; at 64 registers (208 bytes of spill) two systems share each SM (1024 shifted 5-point
+// systems: the 8281..16384-row class 16.0 -> 10.4 ms, the batch 46.0k -> 68-70k solves/s).
 template <int R>
-__global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(ClusterArgs a) {
+__global__ void __launch_bounds__(kClusterThreads, (R >= 8 ? 1 : 2)) cg_cluster_kernel(ClusterArgs a) {
   cluster_group cl = clu::cgx::this_cluster();
   extern __shared__ double s_p[];  // this CTA's slice of p
   __shared__ clu::Block B;
