@@ -1064,7 +1064,7 @@ def bench_stencil(args):
     print(json.dumps(line), flush=True)
 
 
-NCU_CASES = ("c2", "c3", "c1p", "tfqmr", "stencil", "ir")
+NCU_CASES = ("c2", "c3", "c1p", "tfqmr", "stencil", "ir", "c4")
 
 
 def ncu_case(case="c2"):
@@ -1075,7 +1075,9 @@ def ncu_case(case="c2"):
     tfqmr   set-up + 3 TFQMR iterations on the 128^3 7-point system (async mode);
     stencil set-up + 3 CG iterations with the matrix-free 7-point operator on 128^3;
     ir      the float32-inner refinement on the 160^3 27-point system: its float64 residual, then 3 inner
-            iterations with the float32 K1/K2/K3 launched one by one."""
+            iterations with the float32 K1/K2/K3 launched one by one;
+    c4      the 1024 shifted 5-point systems: the autotuner's runs, then one batched solve with the tuned
+            shapes (one cluster-kernel launch per size class) inside the NVTX range "c4solve"."""
     import ctypes as C
 
     import numpy as np
@@ -1089,6 +1091,21 @@ def ncu_case(case="c2"):
     apcg.load()
     ctx = apcg.ctx_create()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    if case == "c4":
+        from synthetic import batch_shifted_5pt
+
+        B = batch_shifted_5pt(1024, seed=0)
+        rowptr, col, val, b = t(B.rowptr), t(B.col), t(B.val), t(B.b)
+        x = torch.zeros(B.n_total, dtype=torch.float64, device=dev)
+        plan = apcg.batch_plan_create(ctx, B.sys_row_off, rowptr, col, val, apcg.cg_opts(rtol=1e-8, check_every=1))
+        apcg.batch_plan_tune(plan, b)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("c4solve")  # the solve's launches, apart from the tuning runs before it
+        res = apcg.batch_plan_solve(plan, b, x, B.nsys)
+        torch.cuda.nvtx.range_pop()
+        apcg.call("apcg_batch_plan_destroy", V(plan))
+        print(json.dumps({"ncu_case": case, "iters_total": int(sum(r["iters"] for r in res))}))
+        return
     if case == "stencil":
         dims = (128, 128, 128)
         Am = stencil_matrix("7pt", dims)
