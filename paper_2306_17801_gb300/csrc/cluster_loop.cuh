@@ -88,9 +88,10 @@ struct NoScalars {
 // (block_sum_quad) into slot `rank` of every CTA of the cluster (remote stores
 // to distributed shared memory, which the cluster barrier's release and
 // acquire make visible), and after the barrier every CTA adds its own C slots
-// in rank order with the same warp tree, so all threads of all CTAs get the
-// same bits without a remote read on the critical path (4096 anisotropic
-// systems, batched refinement: 27.0k -> 28.5k solves/s).
+// in rank order with the same warp tree of log2(C) levels (C is a power of
+// two), so all threads of all CTAs get the same bits without a remote read on
+// the critical path (4096 anisotropic systems, batched refinement: 27.0k ->
+// 28.5k solves/s; the shorter tree: 64^2 CG 6.46 -> 6.30 us per iteration).
 // Slots alternate between two buffers: a buffer is rewritten only two sums
 // later, after a barrier that every CTA passes only once done reading it.
 // scalars(t) runs in thread 0 once the totals are in t[0 .. NV) and may store
@@ -116,7 +117,7 @@ __device__ __forceinline__ void cluster_sum(T (&v)[NV], const Shared& S, int& pa
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       T t = lane < S.C ? (T)S.slot[(parity * kMaxCluster + lane) * 4 + k] : T(0);
-      t = dev::warp_sum(t);
+      for (int o = S.C >> 1; o > 0; o >>= 1) t += __shfl_down_sync(dev::kFull, t, o);  // log2(C) steps
       if (lane == 0) S.tot[k] = (double)t;
     }
     if (lane == 0) scalars(S.tot);
