@@ -134,14 +134,19 @@ apcg_status enqueue_async(apcg_cg_plan P, const double* b, double* x, bool graph
     APCG_CUDA(cudaGraphLaunch(c.exec, s));
     counters().graph_launches++;
   } else {
-    // Launch k iterations at a time and read 'done' after each block.
+    // Launch k iterations at a time and read 'done' after each block.  Each kernel is a programmatic
+    // dependent of the one before it: its launch overlaps its predecessor's last blocks (128^3: 72.2 -> 67.0 us
+    // per iteration; the graph form, whose nodes carry no such edge, 65.1).
     const int64_t max_blocks = (int64_t)c.max_it / c.k + 2;
     int64_t launches = 1;
     for (int64_t blk = 0; blk < max_blocks; ++blk) {
       for (int j = 0; j < c.k; ++j) {
-        APCG_TRY(core_k1(c, x, s, false));
-        APCG_TRY(core_k2(c, x, s, false, 0.0, 0, 0));
-        APCG_TRY(core_k3(c, x, s, false, 0.0));
+        c.pdl = true;
+        apcg_status st1 = core_k1(c, x, s, false);
+        if (st1 == APCG_OK) st1 = core_k2(c, x, s, false, 0.0, 0, 0);
+        if (st1 == APCG_OK) st1 = core_k3(c, x, s, false, 0.0);
+        c.pdl = false;
+        APCG_TRY(st1);
       }
       launches += 3 * c.k;
       count_kernels(3 * c.k);

@@ -95,6 +95,31 @@ Args<T> make_args(const CgCore<T>& c, T* x) {
 
 __device__ __forceinline__ int32_t read_done(const CgState* st) { return *(volatile const int32_t*)&st->done; }
 
+// Entry of a device-scalar iteration kernel: when it was launched as a programmatic dependent of the previous
+// kernel (the launches one by one of the ASYNC mode), wait until that kernel has finished and its writes are
+// visible, then let the next kernel's launch begin while this one runs (its blocks start as this kernel's
+// blocks leave the SMs).  Without a programmatic edge (graph nodes, other launches) both are no-ops.
+__device__ __forceinline__ void dependent_launch_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch configuration of a programmatic dependent launch on stream s.
+struct DependentLaunch {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  DependentLaunch(int grid, size_t dyn_smem, cudaStream_t s) {
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = dyn_smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+};
+
 // The state block copied into shared memory at kernel entry by asynchronous 16-byte copies (cp.async, one
 // per thread of the first warp; the threads do not wait for them), so that the block completing a grid
 // reduction reads the scalars of its epilogue without a round trip to L2 in its serial tail.  The copy is
@@ -194,6 +219,7 @@ __device__ __forceinline__ void k1_finish(const Args<T>& a, T gamma, const CgSta
 // in shared memory by bulk copies, dev::sell_spmv_staged, with stage_smem_bytes of dynamic shared memory)
 template <bool HOST, bool LONG, class T, int G = 8, int CF = dev::kColIndex, bool STAGED = false>
 __global__ void __launch_bounds__(kThreads) k1_kernel(Args<T> a) {
+  if (!HOST) dependent_launch_entry();
   if (!HOST && read_done(a.st)) return;
   // the staged float32 instance keeps no copy: with it the compiler schedules the staged SpMV on 40 instead of
   // 48 registers and the kernel runs about 40% slower (160^3 refinement, inner K1 100.6 -> 142.5 us)
@@ -256,6 +282,7 @@ __global__ void __launch_bounds__(kThreads, 4) k2_kernel(Args<T> a, double alpha
                                                          int32_t use_cond) {
   using VT = typename V16<T>::type;
   constexpr int E = V16<T>::E;
+  if (!HOST) dependent_launch_entry();
   if (!HOST && read_done(a.st)) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
       a.st->body_runs += 1;
@@ -411,6 +438,7 @@ template <bool HOST, class T>
 __global__ void __launch_bounds__(kThreads, 4) k3_kernel(Args<T> a, double beta_host) {
   using VT = typename V16<T>::type;
   constexpr int E = V16<T>::E;
+  if (!HOST) dependent_launch_entry();
   if (!HOST && read_done(a.st)) return;
   const T beta = HOST ? (T)beta_host : (T)a.st->beta;
   const int64_t n = a.n, nv = n / E, stride = (int64_t)gridDim.x * blockDim.x;
@@ -515,6 +543,11 @@ template <bool HOST, class T>
 apcg_status k1_dispatch(const CgCore<T>& c, const Args<T>& a, cudaStream_t s) {
   if (c.S.n > 0) return k1_stencil_dispatch<HOST>(c, a, s);
   void* args[] = {const_cast<Args<T>*>(&a)};
+  if (!HOST && c.pdl) {
+    DependentLaunch L(c.grid_spmv, (size_t)k1_dyn_smem(c), s);
+    APCG_CUDA(cudaLaunchKernelExC(&L.cfg, k1_instance<HOST>(c), args));
+    return APCG_OK;
+  }
   APCG_CUDA(cudaLaunchKernel(k1_instance<HOST>(c), dim3(c.grid_spmv), dim3(kThreads), args, (size_t)k1_dyn_smem(c),
                              s));
   APCG_CUDA(cudaGetLastError());
@@ -559,7 +592,10 @@ apcg_status core_k2(const CgCore<T>& c, T* x, cudaStream_t s, bool host, double 
   const Args<T> a = make_args(c, x);
   if (host)
     k2_kernel<true, T><<<c.grid_vec, kThreads, 0, s>>>(a, alpha, cond, use_cond);
-  else
+  else if (c.pdl) {
+    DependentLaunch L(c.grid_vec, 0, s);
+    APCG_CUDA(cudaLaunchKernelEx(&L.cfg, k2_kernel<false, T>, a, alpha, cond, use_cond));
+  } else
     k2_kernel<false, T><<<c.grid_vec, kThreads, 0, s>>>(a, alpha, cond, use_cond);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;
@@ -570,7 +606,10 @@ apcg_status core_k3(const CgCore<T>& c, T* x, cudaStream_t s, bool host, double 
   const Args<T> a = make_args(c, x);
   if (host)
     k3_kernel<true, T><<<c.grid_vec, kThreads, 0, s>>>(a, beta);
-  else
+  else if (c.pdl) {
+    DependentLaunch L(c.grid_vec, 0, s);
+    APCG_CUDA(cudaLaunchKernelEx(&L.cfg, k3_kernel<false, T>, a, beta));
+  } else
     k3_kernel<false, T><<<c.grid_vec, kThreads, 0, s>>>(a, beta);
   APCG_CUDA(cudaGetLastError());
   return APCG_OK;

@@ -37,6 +37,7 @@ struct CgCore {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   T* graph_x = nullptr;
+  bool pdl = false;  // launch K1-K3 as programmatic dependents of their predecessor (launches one by one)
 };
 
 // Choose the persistent grids for n rows (nnz is informational).  Call after c.A is set.
