@@ -199,7 +199,7 @@ apcg_status finish_async(apcg_cg_plan P) {
   counters().host_syncs++;
   const CgCore<double>& c = P->core;
   if (P->mode == APCG_MODE_ASYNC_GRAPH) {
-    const int64_t n = (int64_t)P->st_host->body_runs * 3 * c.k;
+    const int64_t n = (int64_t)P->st_host->body_runs * 3 * c.body;
     count_kernels(n);
     P->last_launches = 1 + n;
   }

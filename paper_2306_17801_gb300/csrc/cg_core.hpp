@@ -37,6 +37,7 @@ struct CgCore {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   T* graph_x = nullptr;
+  int32_t body = 1;  // iterations captured in one body of the conditional while node
   bool pdl = false;  // launch K1-K3 as programmatic dependents of their predecessor (launches one by one)
 };
 

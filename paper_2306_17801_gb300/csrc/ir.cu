@@ -443,7 +443,7 @@ apcg_status apcg_ir_plan_solve(apcg_ir_plan P, apcg_vec b, apcg_vec x, apcg_ir_r
     counters().d2h_copies++;
     res->inner_total += hi->iter;
     if (k == 0) res->inner_first = hi->iter;
-    launches += (int64_t)hi->body_runs * 3 * P->core.k;
+    launches += (int64_t)hi->body_runs * 3 * P->core.body;
     res->outer = k + 1;
     if (hi->done == kDoneTimeout) {  // a bounded wait in the staged SpMV ran out: the correction is not usable
       res->reason = APCG_BREAKDOWN;

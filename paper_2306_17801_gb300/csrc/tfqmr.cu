@@ -60,7 +60,10 @@ constexpr int kThreads = 256;
 // 16-byte vectors per thread and array in flight in the x updates that follow a ticket (more spill: T1 at
 // 64 registers with 4, the one-entry-at-a-time T2 at 40 registers with more than 2)
 constexpr int kXvT1 = 2, kXvT2 = 4, kXvT2Single = 2;
-constexpr int kClusterMaxRows = 16384;  // the whole-solve cluster kernel: 16 CTAs x 512 threads x 2 rows
+constexpr int kClusterMaxRows = 16384;
+// Iterations per body of the graph's conditional while node: k, or the smallest multiple of k of at least this
+// many (each K2/T2 still tests at its own iteration count; the while node itself costs about 4 us per body)
+constexpr int kMinGraphBody = 8;  // the whole-solve cluster kernel: 16 CTAs x 512 threads x 2 rows
 
 // Device-resident scalars of one TFQMR solve.
 struct TqState {
@@ -445,6 +448,7 @@ struct apcg_tfqmr_plan_s {
   int32_t mode = APCG_MODE_ASYNC_GRAPH;
   apcg::tq::TqArgs a{};  // x is filled in per solve
   int32_t n = 0, k = 1, max_it = 0, hist_len = 0;
+  int32_t body = 1;  // iterations captured in one body of the conditional while node
   int grid_spmv = 1, grid_vec = 1, grid_t3 = 1;  // t3 takes fewer registers than t2: its own persistent grid
   bool long_rows = false;  // the set-up kernels' SpMV path
   int group = 0;           // the iteration kernels' SpMV group size (0: one entry at a time)
@@ -724,9 +728,10 @@ apcg_status build_graph(Plan P, double* x) {
   APCG_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   const HostScalars none{};
   apcg_status st = APCG_OK;
-  for (int j = 0; j < P->k && st == APCG_OK; ++j) {
+  P->body = P->k >= kMinGraphBody ? P->k : P->k * ((kMinGraphBody + P->k - 1) / P->k);
+  for (int j = 0; j < P->body && st == APCG_OK; ++j) {
     st = launch_t1(P, x, P->cap_stream, false, none);
-    if (st == APCG_OK) st = launch_t2(P, x, P->cap_stream, false, none, hnd, j == P->k - 1 ? 1 : 0);
+    if (st == APCG_OK) st = launch_t2(P, x, P->cap_stream, false, none, hnd, j == P->body - 1 ? 1 : 0);
     if (st == APCG_OK) st = launch_t3(P, x, P->cap_stream, false, none);
   }
   cudaGraph_t captured = nullptr;
@@ -806,7 +811,7 @@ apcg_status finish_async(Plan P) {
   APCG_CUDA(cudaStreamSynchronize(P->ctx->stream));
   counters().host_syncs++;
   if (P->mode == APCG_MODE_ASYNC_GRAPH) {
-    const int64_t body = (int64_t)P->st_host->body_runs * 3 * P->k;
+    const int64_t body = (int64_t)P->st_host->body_runs * 3 * P->body;
     count_kernels(body);
     P->last_launches += body;
   }
